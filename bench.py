@@ -1,0 +1,375 @@
+"""Benchmark: CSR SpMV by speculative segmented sum on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload stencil160] [--tile-w 0] [--tile-s 0] [--e2e-steps 20]
+
+A step is one full y = A x through ssspmv_csr_f64 (kernels (a) partition,
+(b) segmented sum, (c) calibration) on the synthetic 27-point stencil over a
+160^3 grid in FP64 (m = 4,096,000, nnz = 109,215,352), inputs resident in
+HBM.  L2 is flushed (a 512 MB write) between timed steps, outside the timed
+events.  value = algorithmic bytes / time, bytes = nnz*(8+4) + (m+1)*4 +
+m*8 + n*8 (x read once), in GB/s.  Under torchrun each rank runs an
+independent replica (the path needs no exchange); value sums all ranks'
+bytes over the slowest rank's time.
+
+--impl reference times the CPU oracle (rows split over OpenMP threads, the
+paper's CPU row-block method) on this machine's host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SpMV effective GB/s & % of HBM peak vs plain FP64 kernel, at stated error"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def algorithmic_bytes(m: int, n: int, nnz: int, val_bytes: int = 8, idx_bytes: int = 4,
+                      y_bytes: int = 8, x_bytes: int = 8) -> int:
+    """nnz*(val+idx) + (m+1)*idx + m*y + n*x (x counted once)."""
+    return nnz * (val_bytes + idx_bytes) + (m + 1) * idx_bytes + m * y_bytes + n * x_bytes
+
+
+def paper_bytes(m: int, nnz: int, val_bytes: int = 8, idx_bytes: int = 4) -> int:
+    """The paper's bandwidth numerator (Sec. 4.3): (m+1+nnz)*idx + (2nnz+m)*val."""
+    return (m + 1 + nnz) * idx_bytes + (2 * nnz + m) * val_bytes
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1504_06474_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from profiles/traffic.json, only if it
+    was captured from the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    for rec in d.get("records", []):
+        if (rec.get("kernel") == kernel and rec.get("workload") == workload
+                and rec.get("source_digest") == source_digest()):
+            return rec.get("dram_bytes_per_launch")
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = open(os.devnull, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        self.proc.terminate()
+        try:
+            text, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            text, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in text.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_rate(A, x, budget_s: float, max_reps: int = 1000):
+    """Times the oracle's OpenMP row loop over the whole matrix, repeated until
+    budget_s of CPU time has been spent.  Returns (GB/s, threads, reps, s)."""
+    import numpy as np
+
+    import oracle
+    y = np.empty(A.m)
+    oracle.spmv_omp(A.row_ptr, A.col, A.val, x, y=y)  # warm caches and threads
+    reps, used, t0 = 0, 1, time.perf_counter()
+    while reps < max_reps:
+        _, used = oracle.spmv_omp(A.row_ptr, A.col, A.val, x, y=y)
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    nbytes = algorithmic_bytes(A.m, A.n, A.nnz)
+    return nbytes * reps / dt / 1e9, used, reps, dt
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import synth
+    import oracle
+    oracle.build()
+    A, x = synth.workload(args.workload)
+    rate_w, used, reps, _ = cpu_oracle_rate(A, x, budget_s=1.0, max_reps=max(1, args.warmup))
+    import numpy as np
+    y = np.empty(A.m)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, used = oracle.spmv_omp(A.row_ptr, A.col, A.val, x, y=y)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    nbytes = algorithmic_bytes(A.m, A.n, A.nnz)
+    value = nbytes / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t * 1e3, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "m": A.m, "n": A.n, "nnz": A.nnz,
+                   "bytes_per_step": nbytes},
+        "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": used,
+                         "kind": "oracle",
+                         "sample": "the whole %s SpMV per step (oracle row loop, rows split "
+                                   "over %d OpenMP threads)" % (args.workload, used)},
+        "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import synth
+    from paper_1504_06474_gb300 import _build, api
+    from paper_1504_06474_gb300 import ssspmv as C
+    if rank == 0 or world == 1:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+
+    A, x = synth.workload(args.workload)
+    Ad = api.to_device(A.row_ptr, A.col, A.val, A.n, dev)
+    xd = torch.as_tensor(x, device=dev)
+    y = torch.empty(A.m, dtype=torch.float64, device=dev)
+    shape = C.ssspmv_plan_shape(A.m, A.nnz, 8, C.make_opts(W=args.tile_w, S=args.tile_s))
+    ws = api.workspace_for(Ad, C.make_opts(W=args.tile_w, S=args.tile_s), device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(opts):
+        rc = C.ssspmv_csr_f64(A.m, A.n, A.nnz, Ad.row_ptr, Ad.col, Ad.val, xd, y, opts=opts,
+                              workspace=ws, stream=stream)
+        if rc != 0:
+            raise C.SsspmvError(rc, "ssspmv_csr_f64")
+
+    plain = C.make_opts(W=args.tile_w, S=args.tile_s)
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(plain)
+    torch.cuda.synchronize(dev)
+
+    # per-step events recorded by the library on the launching stream
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    arrs = [(ctypes.c_void_p * 4)(*[e.cuda_event for e in row]) for row in evs]
+    opts_k = [C.make_opts(W=args.tile_w, S=args.tile_s, stage_events=ctypes.addressof(a))
+              for a in arrs]
+    for row in evs:  # materialise the CUDA events
+        for e in row:
+            e.record(stream)
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    time.sleep(0.25)
+    t_wall = time.perf_counter()
+    for k in range(K):
+        flush.zero_()
+        step(opts_k[k])
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+
+    per_step = [evs[k][0].elapsed_time(evs[k][3]) for k in range(K)]       # ms
+    seg = [evs[k][1].elapsed_time(evs[k][2]) for k in range(K)]
+    part = [evs[k][0].elapsed_time(evs[k][1]) for k in range(K)]
+    cal = [evs[k][2].elapsed_time(evs[k][3]) for k in range(K)]
+    t_total = sum(per_step) / 1e3                                            # s
+    if world > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    nbytes = algorithmic_bytes(A.m, A.n, A.nnz)
+    value = nbytes * K * world / t_total / 1e9
+    ms_step = t_total / K * 1e3
+
+    # end to end through the host-buffer entry point: H2D of row_ptr, col,
+    # val, x from pinned memory, the product, D2H of y, every step
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        h_rp, h_col, h_val, h_x = pin(A.row_ptr), pin(A.col), pin(A.val), pin(x)
+        h_y = torch.empty(A.m, dtype=torch.float64).pin_memory()
+        nbuf = C.ssspmv_host_buffer_bytes(A.m, A.n, A.nnz, plain)
+        del flush
+        buf = torch.empty(nbuf, dtype=torch.uint8, device=dev)
+        for _ in range(2):
+            C.check(C.ssspmv_csr_f64_host(A.m, A.n, A.nnz, h_rp, h_col, h_val, h_x, h_y,
+                                          opts=plain, dev_buffer=buf, stream=stream),
+                    "ssspmv_csr_f64_host")
+        tt0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            C.check(C.ssspmv_csr_f64_host(A.m, A.n, A.nnz, h_rp, h_col, h_val, h_x, h_y,
+                                          opts=plain, dev_buffer=buf, stream=stream),
+                    "ssspmv_csr_f64_host")
+        te = (time.perf_counter() - tt0) / args.e2e_steps
+        if world > 1:
+            tt = torch.tensor([te], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        assert np.array_equal(h_y.numpy(), y.cpu().numpy())
+        h2d = (A.m + 1) * 4 + A.nnz * 4 + A.nnz * 8 + A.n * 8
+        e2e = {"value": round(nbytes * world / te / 1e9, 3), "unit": "GB/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": A.m * 8,
+               "ms_per_step": round(te * 1e3, 4)}
+
+    status = C.ssspmv_device_status(ws, stream=stream)
+    if status:
+        raise RuntimeError("device status bits %#x" % status)
+
+    hbm, peak_kind = peaks()
+    seg_ms = sum(seg) / K
+    achieved = nbytes / (seg_ms / 1e3) / 1e9
+    traffic = ncu_traffic("segsum_kernel", args.workload)
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and args.cpu_seconds > 0:
+            rate, used, reps, dt = cpu_oracle_rate(A, x, budget_s=args.cpu_seconds)
+            cpu = {"value": round(rate, 3), "unit": "GB/s", "cores": used, "kind": "oracle",
+                   "sample": "%d whole %s SpMVs (oracle row loop over %d OpenMP threads), "
+                             "%.1f s" % (reps, args.workload, used, dt)}
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "m": A.m, "n": A.n, "nnz": A.nnz,
+                       "W": shape["W"], "L": shape["L"], "S": shape["S"],
+                       "bunches": shape["nbunches"], "bytes_per_step": nbytes,
+                       "paper_bytes_per_step": paper_bytes(A.m, A.nnz),
+                       "hbm_frac": round(value / world / hbm, 4),
+                       "gflops": round(2.0 * A.nnz * K * world / t_total / 1e9, 3),
+                       "l2": "flushed between steps (512 MB write, outside the timed events)",
+                       "stage_ms": {"partition": round(sum(part) / K, 5),
+                                    "segsum": round(seg_ms, 5),
+                                    "calibrate": round(sum(cal) / K, 5)},
+                       "wall_s_timed_loop": round(t_wall, 3)},
+            "roofline": {"bound": "hbm", "kernel": "segsum_kernel",
+                         "achieved": round(achieved, 2), "peak": hbm, "unit": "GB/s",
+                         "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
+                         "traffic": traffic},
+            "clocks": clocks,
+            "e2e": e2e,
+            "gpu_launches": 3 * K,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="stencil160")
+    ap.add_argument("--tile-w", type=int, default=0)
+    ap.add_argument("--tile-s", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

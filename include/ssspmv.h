@@ -1,0 +1,151 @@
+/*
+ * ssspmv.h -- C ABI of a GB300 (sm_103a) CSR sparse matrix-vector multiply
+ * computed as a speculative segmented sum (Liu & Vinter, "Speculative
+ * Segmented Sum for Sparse Matrix-Vector Multiplication on Heterogeneous
+ * Processors").
+ *
+ * The operation is y = A x for an m x n matrix A in CSR form (Sec. 2.1):
+ *   row_ptr[m+1], col_idx[nnz], val[nnz], x[n] -> y[m]
+ * with y overwritten (no alpha/beta) and every row written, empty rows as 0.
+ *
+ * The nonzeros are cut into tiles of L = 32*W entries (Sec. 3.1: T = 32 lanes
+ * of a warp, W entries per lane); a warp ("thread-bunch") processes S
+ * consecutive tiles.  Three kernels run on the caller's stream:
+ *   (a) partition: tile_offset[t] = the largest r with row_ptr[r] <= t*L
+ *       (Sec. 3.2 and Algorithm 1: binary search, rightmost match);
+ *   (b) segmented sum: per tile, the row-start descriptor is built on chip
+ *       from row_ptr, products val*x[col] are reduced per segment, and each
+ *       segment s is stored speculatively to y[tile_offset[t] + s]; the first
+ *       segment of each bunch goes to a synchronizer record (Sec. 3.2,
+ *       Algorithm 1);
+ *   (c) calibration: synchronizer records are summed into their rows, the
+ *       partials of tiles holding empty rows ("dirty" tiles) are moved to
+ *       their true rows, and empty rows are zeroed (Sec. 3.2, checking
+ *       prediction, and Algorithm 1's synchronization step, here on the GPU).
+ *
+ * Conventions for every entry point below:
+ *   - Array pointers are DEVICE pointers unless the name says host, owned by
+ *     the caller; the library never frees caller memory.  Calls are
+ *     asynchronous on `stream` (a cudaStream_t passed as void*, NULL = the
+ *     legacy default stream); inputs must stay valid until it completes.
+ *   - Indices are 0-based int32 (the paper's idx_type, Sec. 4.3); nnz must fit
+ *     in int32.  Column order inside a row is free; duplicates are summed.
+ *   - `val` and `col_idx` must be 16-byte aligned (they are streamed by bulk
+ *     asynchronous copies); x and y need only natural alignment.
+ *   - Column indices must lie in [0, n); with opts->validate == 0 an
+ *     out-of-range column is undefined behaviour (call ssspmv_validate_csr
+ *     first for untrusted input).
+ *   - Return value: SSSPMV_OK (0) or a negative code; nothing is launched
+ *     when a host-side check fails.  No C++ exception crosses the ABI.
+ *   - The same input gives bit-identical y on every run (no floating-point
+ *     atomics; all reductions have a fixed order).
+ */
+#ifndef SSSPMV_H
+#define SSSPMV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SSSPMV_OK            0
+#define SSSPMV_EINVAL       -1  /* bad scalar, null pointer with size > 0, misalignment, bad opts */
+#define SSSPMV_EWORKSPACE   -2  /* workspace NULL or smaller than ssspmv_workspace_bytes() */
+#define SSSPMV_ECUDA        -3  /* a CUDA call failed; see ssspmv_last_cuda_error() */
+#define SSSPMV_EDEVICE      -4  /* a kernel reported an inconsistency or a timed-out wait */
+#define SSSPMV_EUNSUPPORTED -5  /* tile shape not compiled in this build */
+
+/* Device error bits written by the kernels into the workspace (read with
+ * ssspmv_device_status). */
+#define SSSPMV_DEV_TIMEOUT   1u  /* a bounded wait on a bulk copy gave up */
+#define SSSPMV_DEV_RANGE     2u  /* a computed row index fell outside [0, m) */
+#define SSSPMV_DEV_CALIB     4u  /* calibration found a segment count that does not match row_ptr */
+
+/* Tile and launch parameters (Sec. 3.1, Table 3).  Zero-initialise and set
+ * only what you need; a NULL opts pointer means all defaults. */
+typedef struct ssspmv_opts {
+    int32_t W;         /* entries per lane (odd, see ssspmv_supported_w); L = 32*W.
+                          0 = pick from the mean row length nnz/m */
+    int32_t S;         /* tiles per thread-bunch (warp); 0 = one wave of warps */
+    int32_t validate;  /* reserved, must be 0 (use ssspmv_validate_csr) */
+    int32_t reserved;
+    void   *stage_events; /* optional cudaEvent_t[4] (as void*): recorded on the
+                             stream before kernel (a), before (b), before (c)
+                             and after (c); NULL = none */
+} ssspmv_opts;
+
+/* The tile shape and bunch count a call with these arguments would use.
+ * val_bytes = sizeof the stored value type (8 for FP64).  Any output pointer
+ * may be NULL.  Returns SSSPMV_OK or SSSPMV_EINVAL/EUNSUPPORTED. */
+int ssspmv_plan_shape(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_opts *opts,
+                      int32_t *W, int32_t *L, int32_t *S, int64_t *ntiles, int64_t *nbunches);
+
+/* Bytes of device workspace needed by a call with these arguments
+ * (tile offsets, per-tile info, synchronizer records; the paper's
+ * pre-allocated containers, Sec. 3.3).  Returns 0 on invalid arguments. */
+size_t ssspmv_workspace_bytes(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_opts *opts);
+
+/* y = A x in FP64 (val, x, y double).  workspace: device buffer of at least
+ * ssspmv_workspace_bytes(m, nnz, 8, opts) bytes, 256-byte aligned, not used
+ * by another call in flight.  Kernels: (a), (b), (c) above. */
+int ssspmv_csr_f64(int32_t m, int32_t n, int32_t nnz,
+                   const int32_t *row_ptr, const int32_t *col_idx, const double *val,
+                   const double *x, double *y,
+                   const ssspmv_opts *opts, void *workspace, size_t ws_bytes, void *stream);
+
+/* The same product with HOST arrays (pageable or pinned): copies row_ptr,
+ * col_idx, val and x into `dev_buffer` (device memory of at least
+ * ssspmv_host_buffer_bytes() bytes), runs ssspmv_csr_f64 on `stream`, copies
+ * y back to host_y and synchronises the stream before returning. */
+size_t ssspmv_host_buffer_bytes(int32_t m, int32_t n, int32_t nnz, const ssspmv_opts *opts);
+int ssspmv_csr_f64_host(int32_t m, int32_t n, int32_t nnz,
+                        const int32_t *host_row_ptr, const int32_t *host_col_idx,
+                        const double *host_val, const double *host_x, double *host_y,
+                        const ssspmv_opts *opts, void *dev_buffer, size_t dev_bytes,
+                        void *stream);
+
+/* FP64 product that also exports the method's index artefacts for checking
+ * against an independent derivation (any output may be NULL):
+ *   tile_offset[ntiles+1]   kernel (a)'s partition (Sec. 3.2)
+ *   desc[ntiles*W]          raw segment descriptor words of kernel (b): bit k
+ *                           of tile t is bit k%32 of word t*W + k/32, set iff a
+ *                           row starts at entry t*L + k (bit 0 NOT forced)
+ *   tile_info[ntiles]       bit 31 = dirty (an empty row in [start, stop)),
+ *                           bits 0..30 = number of segments of the tile
+ *   sync_idx[nbunches]      synchronizer row of each bunch (= tile_offset[w*S])
+ *   y_spec[m]               y after kernel (b), before calibration (entries
+ *                           kernel (b) does not write are left as y held them)
+ * Synchronises the stream and returns SSSPMV_EDEVICE if a kernel flagged an
+ * error. */
+int ssspmv_csr_f64_debug(int32_t m, int32_t n, int32_t nnz,
+                         const int32_t *row_ptr, const int32_t *col_idx, const double *val,
+                         const double *x, double *y,
+                         const ssspmv_opts *opts, void *workspace, size_t ws_bytes, void *stream,
+                         int32_t *tile_offset, uint32_t *desc, uint32_t *tile_info,
+                         int32_t *sync_idx, double *y_spec);
+
+/* Checks a CSR structure on the device: row_ptr[0] == 0, row_ptr[m] == nnz,
+ * row_ptr non-decreasing, 0 <= col_idx < n.  `scratch` is 16 bytes of device
+ * memory.  Synchronises the stream.  Returns SSSPMV_OK or SSSPMV_EINVAL. */
+int ssspmv_validate_csr(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr,
+                        const int32_t *col_idx, void *scratch, void *stream);
+
+/* Device error bits (SSSPMV_DEV_*) accumulated in this workspace since it was
+ * last cleared; synchronises the stream.  clear != 0 resets them. */
+int ssspmv_device_status(void *workspace, size_t ws_bytes, void *stream, int clear,
+                         uint32_t *bits);
+
+/* Odd W values compiled into this build, written to out[0..*count). */
+int ssspmv_supported_w(int32_t *out, int32_t cap, int32_t *count);
+
+const char *ssspmv_strerror(int code);
+int ssspmv_last_cuda_error(void);     /* cudaError_t of the last failed CUDA call */
+int ssspmv_version(void);             /* major*10000 + minor*100 + patch */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSSPMV_H */

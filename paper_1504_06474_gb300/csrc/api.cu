@@ -1,0 +1,349 @@
+// api.cu -- the extern "C" boundary declared in include/ssspmv.h: argument
+// checks, tile-shape resolution, workspace carve-up and dispatch to the
+// per-precision launchers.  No exception crosses the boundary.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "launch.cuh"
+
+namespace ssspmv {
+
+int f64_supported_w(int32_t *out, int cap);
+int f64_resolve(Layout &l, int32_t S_opt);
+int f64_run(Call &c);
+
+static thread_local int g_last_cuda_error = 0;
+
+int record_cuda_error(cudaError_t e)
+{
+    g_last_cuda_error = (int)e;
+    return SSSPMV_ECUDA;
+}
+
+int device_sm_count()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        (void)cudaGetLastError();
+        return 152;
+    }
+    if (cache[dev] > 0) return cache[dev];
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+        (void)cudaGetLastError();
+        return 152;
+    }
+    cache[dev] = n;
+    return n;
+}
+
+// W from the options, or from the mean row length (odd, snapped to the
+// nearest compiled shape): lanes then tend to start at row heads, which keeps
+// the x gathers of one warp instruction on neighbouring rows.
+static int resolve_w(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_opts *o, int32_t *W)
+{
+    int32_t ws[16];
+    int n = 0;
+    if (val_bytes == 8) n = f64_supported_w(ws, 16);
+    if (n <= 0) return SSSPMV_EUNSUPPORTED;
+    if (n > 16) n = 16;
+    if (o && o->W != 0) {
+        for (int i = 0; i < n; ++i)
+            if (ws[i] == o->W) { *W = o->W; return SSSPMV_OK; }
+        return o->W < 0 ? SSSPMV_EINVAL : SSSPMV_EUNSUPPORTED;
+    }
+    const double mean = m > 0 ? (double)nnz / (double)m : 0.0;
+    int best = ws[0];
+    double bd = 1e300;
+    for (int i = 0; i < n; ++i) {
+        const double d = std::fabs((double)ws[i] - mean);
+        if (d < bd) { bd = d; best = ws[i]; }
+    }
+    *W = best;
+    return SSSPMV_OK;
+}
+
+// device-independent part of the layout: tile shape, tile count, bunch cap
+static int make_layout(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_opts *o, Layout &l)
+{
+    if (m < 0 || nnz < 0) return SSSPMV_EINVAL;
+    if (o && (o->S < 0 || o->validate != 0)) return SSSPMV_EINVAL;
+    int32_t W = 0;
+    int rc = resolve_w(m, nnz, val_bytes, o, &W);
+    if (rc) return rc;
+    l.W = W;
+    l.L = 32 * W;
+    l.ntiles = ((int64_t)nnz + l.L - 1) / l.L;
+    const int32_t S_opt = o ? o->S : 0;
+    if (S_opt > 0) {
+        l.nbunch_cap = (l.ntiles + S_opt - 1) / S_opt;
+    } else {
+        l.nbunch_cap = l.ntiles < kMaxAutoBunches ? l.ntiles : kMaxAutoBunches;
+    }
+    carve(l);
+    return SSSPMV_OK;
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+static int check_csr_args(int32_t m, int32_t n, int32_t nnz, const void *row_ptr,
+                          const void *col, const void *val, const void *x, const void *y)
+{
+    if (m < 0 || n < 0 || nnz < 0) return SSSPMV_EINVAL;
+    if (m == 0 && nnz != 0) return SSSPMV_EINVAL;
+    if (m > 0 && (!row_ptr || !y)) return SSSPMV_EINVAL;
+    if (nnz > 0 && (!col || !val || !x || n == 0)) return SSSPMV_EINVAL;
+    if (nnz > 0 && (!aligned16(col) || !aligned16(val))) return SSSPMV_EINVAL;
+    return SSSPMV_OK;
+}
+
+static int run_f64_call(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr,
+                        const int32_t *col, const double *val, const double *x, double *y,
+                        const ssspmv_opts *opts, void *ws, size_t ws_bytes, void *stream,
+                        uint32_t *dbg_desc, double *dbg_yspec, Layout *out_layout)
+{
+    int rc = check_csr_args(m, n, nnz, row_ptr, col, val, x, y);
+    if (rc) return rc;
+    Layout l;
+    rc = make_layout(m, nnz, 8, opts, l);
+    if (rc) return rc;
+    if (out_layout) *out_layout = l;
+    if (m == 0) return SSSPMV_OK;
+    if (!ws || ws_bytes < l.total || ((uintptr_t)ws & 255u)) return SSSPMV_EWORKSPACE;
+    rc = f64_resolve(l, opts ? opts->S : 0);
+    if (rc) return rc;
+    if (l.nbunches > l.nbunch_cap) return SSSPMV_EWORKSPACE;
+    if (out_layout) *out_layout = l;
+    Call c;
+    c.m = m;
+    c.n = n;
+    c.nnz = nnz;
+    c.row_ptr = row_ptr;
+    c.col = col;
+    c.val = val;
+    c.x = x;
+    c.y = y;
+    c.lay = l;
+    c.ws = static_cast<unsigned char *>(ws);
+    c.stream = static_cast<cudaStream_t>(stream);
+    c.ev = (opts && opts->stage_events) ? static_cast<cudaEvent_t *>(opts->stage_events) : nullptr;
+    c.dbg_desc = dbg_desc;
+    c.dbg_yspec = dbg_yspec;
+    return f64_run(c);
+}
+
+// ---------------------------------------------------------------------------
+// CSR structure check (used by ssspmv_validate_csr)
+
+__global__ void validate_kernel(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr,
+                                const int32_t *col, uint32_t *bad)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i0 == 0 && (row_ptr[0] != 0 || row_ptr[m] != nnz)) atomicOr(bad, 1u);
+    for (int64_t r = i0; r < m; r += stride)
+        if (row_ptr[r + 1] < row_ptr[r]) atomicOr(bad, 2u);
+    for (int64_t k = i0; k < nnz; k += stride) {
+        const int32_t c = col[k];
+        if (c < 0 || c >= n) atomicOr(bad, 4u);
+    }
+}
+
+}  // namespace ssspmv
+
+using namespace ssspmv;
+
+extern "C" {
+
+int ssspmv_version(void) { return 10000; }
+
+int ssspmv_last_cuda_error(void) { return g_last_cuda_error; }
+
+const char *ssspmv_strerror(int code)
+{
+    switch (code) {
+    case SSSPMV_OK: return "success";
+    case SSSPMV_EINVAL: return "invalid argument";
+    case SSSPMV_EWORKSPACE: return "workspace missing, misaligned or too small";
+    case SSSPMV_ECUDA: return "CUDA error (see ssspmv_last_cuda_error)";
+    case SSSPMV_EDEVICE: return "a kernel reported an error";
+    case SSSPMV_EUNSUPPORTED: return "tile shape not compiled in this build";
+    default: return "unknown error";
+    }
+}
+
+int ssspmv_supported_w(int32_t *out, int32_t cap, int32_t *count)
+{
+    int32_t tmp[16];
+    int n = f64_supported_w(tmp, 16);
+    if (count) *count = n;
+    if (out)
+        for (int i = 0; i < n && i < cap; ++i) out[i] = tmp[i];
+    return SSSPMV_OK;
+}
+
+int ssspmv_plan_shape(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_opts *opts,
+                      int32_t *W, int32_t *L, int32_t *S, int64_t *ntiles, int64_t *nbunches)
+{
+    if (val_bytes != 8) return SSSPMV_EUNSUPPORTED;
+    Layout l;
+    int rc = make_layout(m, nnz, val_bytes, opts, l);
+    if (rc) return rc;
+    rc = f64_resolve(l, opts ? opts->S : 0);
+    if (rc) return rc;
+    if (W) *W = l.W;
+    if (L) *L = l.L;
+    if (S) *S = l.S;
+    if (ntiles) *ntiles = l.ntiles;
+    if (nbunches) *nbunches = l.nbunches;
+    return SSSPMV_OK;
+}
+
+size_t ssspmv_workspace_bytes(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_opts *opts)
+{
+    if (val_bytes != 8) return 0;
+    Layout l;
+    if (make_layout(m, nnz, val_bytes, opts, l)) return 0;
+    return l.total;
+}
+
+int ssspmv_csr_f64(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr,
+                   const int32_t *col_idx, const double *val, const double *x, double *y,
+                   const ssspmv_opts *opts, void *workspace, size_t ws_bytes, void *stream)
+{
+    return run_f64_call(m, n, nnz, row_ptr, col_idx, val, x, y, opts, workspace, ws_bytes,
+                        stream, nullptr, nullptr, nullptr);
+}
+
+int ssspmv_csr_f64_debug(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr,
+                         const int32_t *col_idx, const double *val, const double *x, double *y,
+                         const ssspmv_opts *opts, void *workspace, size_t ws_bytes, void *stream,
+                         int32_t *tile_offset, uint32_t *desc, uint32_t *tile_info,
+                         int32_t *sync_idx, double *y_spec)
+{
+    Layout l;
+    int rc = run_f64_call(m, n, nnz, row_ptr, col_idx, val, x, y, opts, workspace, ws_bytes,
+                          stream, desc, y_spec, &l);
+    if (rc) return rc;
+    if (m == 0) return SSSPMV_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    cudaError_t e = cudaSuccess;
+    if (tile_offset && e == cudaSuccess)
+        e = cudaMemcpyAsync(tile_offset, ws + l.off_tile_offset,
+                            sizeof(int32_t) * (size_t)(l.ntiles + 1), cudaMemcpyDeviceToDevice, s);
+    if (tile_info && l.ntiles > 0 && e == cudaSuccess)
+        e = cudaMemcpyAsync(tile_info, ws + l.off_tile_info, sizeof(uint32_t) * (size_t)l.ntiles,
+                            cudaMemcpyDeviceToDevice, s);
+    if (sync_idx && l.nbunches > 0 && e == cudaSuccess)
+        e = cudaMemcpyAsync(sync_idx, ws + l.off_sync_idx, sizeof(int32_t) * (size_t)l.nbunches,
+                            cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return record_cuda_error(e);
+    uint32_t bits = 0;
+    rc = ssspmv_device_status(workspace, ws_bytes, stream, 0, &bits);
+    if (rc) return rc;
+    return bits ? SSSPMV_EDEVICE : SSSPMV_OK;
+}
+
+int ssspmv_device_status(void *workspace, size_t ws_bytes, void *stream, int clear,
+                         uint32_t *bits)
+{
+    if (!workspace || ws_bytes < 16) return SSSPMV_EWORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, workspace, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && clear) e = cudaMemsetAsync(workspace, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return record_cuda_error(e);
+    if (bits) *bits = h;
+    return SSSPMV_OK;
+}
+
+size_t ssspmv_host_buffer_bytes(int32_t m, int32_t n, int32_t nnz, const ssspmv_opts *opts)
+{
+    if (m < 0 || n < 0 || nnz < 0) return 0;
+    size_t ws = ssspmv_workspace_bytes(m, nnz, 8, opts);
+    if (ws == 0) return 0;
+    size_t o = 0;
+    o = align256(o + sizeof(int32_t) * ((size_t)m + 1));
+    o = align256(o + sizeof(int32_t) * (size_t)nnz);
+    o = align256(o + sizeof(double) * (size_t)nnz);
+    o = align256(o + sizeof(double) * (size_t)n);
+    o = align256(o + sizeof(double) * (size_t)m);
+    return o + ws;
+}
+
+int ssspmv_csr_f64_host(int32_t m, int32_t n, int32_t nnz, const int32_t *host_row_ptr,
+                        const int32_t *host_col_idx, const double *host_val,
+                        const double *host_x, double *host_y, const ssspmv_opts *opts,
+                        void *dev_buffer, size_t dev_bytes, void *stream)
+{
+    int rc = check_csr_args(m, n, nnz, host_row_ptr, host_col_idx, host_val, host_x, host_y);
+    if (rc && rc != SSSPMV_EINVAL) return rc;
+    if (m < 0 || n < 0 || nnz < 0 || (m == 0 && nnz != 0)) return SSSPMV_EINVAL;
+    if (m > 0 && (!host_row_ptr || !host_y)) return SSSPMV_EINVAL;
+    if (nnz > 0 && (!host_col_idx || !host_val || !host_x || n == 0)) return SSSPMV_EINVAL;
+    if (m == 0) return SSSPMV_OK;
+    const size_t need = ssspmv_host_buffer_bytes(m, n, nnz, opts);
+    if (need == 0) return SSSPMV_EINVAL;
+    if (!dev_buffer || dev_bytes < need || ((uintptr_t)dev_buffer & 255u))
+        return SSSPMV_EWORKSPACE;
+    unsigned char *p = static_cast<unsigned char *>(dev_buffer);
+    size_t o = 0;
+    int32_t *d_rp = reinterpret_cast<int32_t *>(p + o);
+    o = align256(o + sizeof(int32_t) * ((size_t)m + 1));
+    int32_t *d_col = reinterpret_cast<int32_t *>(p + o);
+    o = align256(o + sizeof(int32_t) * (size_t)nnz);
+    double *d_val = reinterpret_cast<double *>(p + o);
+    o = align256(o + sizeof(double) * (size_t)nnz);
+    double *d_x = reinterpret_cast<double *>(p + o);
+    o = align256(o + sizeof(double) * (size_t)n);
+    double *d_y = reinterpret_cast<double *>(p + o);
+    o = align256(o + sizeof(double) * (size_t)m);
+    void *ws = p + o;
+    const size_t ws_bytes = dev_bytes - o;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(d_rp, host_row_ptr, sizeof(int32_t) * ((size_t)m + 1),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nnz > 0)
+        e = cudaMemcpyAsync(d_col, host_col_idx, sizeof(int32_t) * (size_t)nnz,
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nnz > 0)
+        e = cudaMemcpyAsync(d_val, host_val, sizeof(double) * (size_t)nnz, cudaMemcpyHostToDevice,
+                            s);
+    if (e == cudaSuccess && n > 0)
+        e = cudaMemcpyAsync(d_x, host_x, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return record_cuda_error(e);
+    rc = ssspmv_csr_f64(m, n, nnz, d_rp, d_col, d_val, d_x, d_y, opts, ws, ws_bytes, stream);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(host_y, d_y, sizeof(double) * (size_t)m, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return record_cuda_error(e);
+    return SSSPMV_OK;
+}
+
+int ssspmv_validate_csr(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr,
+                        const int32_t *col_idx, void *scratch, void *stream)
+{
+    if (m < 0 || n < 0 || nnz < 0 || !scratch) return SSSPMV_EINVAL;
+    if (m > 0 && !row_ptr) return SSSPMV_EINVAL;
+    if (nnz > 0 && !col_idx) return SSSPMV_EINVAL;
+    if (m == 0) return nnz == 0 ? SSSPMV_OK : SSSPMV_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t *bad = static_cast<uint32_t *>(scratch);
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return record_cuda_error(e);
+    validate_kernel<<<4 * device_sm_count(), 256, 0, s>>>(m, n, nnz, row_ptr, col_idx, bad);
+    e = cudaGetLastError();
+    uint32_t h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return record_cuda_error(e);
+    return h ? SSSPMV_EINVAL : SSSPMV_OK;
+}
+
+}  // extern "C"

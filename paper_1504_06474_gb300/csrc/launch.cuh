@@ -1,0 +1,162 @@
+// launch.cuh -- host-side launch of kernels (a), (b), (c) for one precision.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "layout.h"
+#include "segsum.cuh"
+
+namespace ssspmv {
+
+struct Call {
+    int32_t m = 0, n = 0, nnz = 0;
+    const int32_t *row_ptr = nullptr;
+    const int32_t *col = nullptr;
+    const void *val = nullptr;
+    const void *x = nullptr;
+    void *y = nullptr;
+    Layout lay;
+    unsigned char *ws = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t *ev = nullptr;       // 4 events or null
+    uint32_t *dbg_desc = nullptr;    // ntiles*W words or null
+    void *dbg_yspec = nullptr;       // m values or null
+};
+
+int record_cuda_error(cudaError_t e);  // api.cu: remembers e, returns SSSPMV_ECUDA
+int device_sm_count();                 // api.cu: SMs of the current device (cached)
+
+constexpr int kZeroBlocks = 32;
+
+// resident warps per SM of kernel (b) for this tile shape (cached per device)
+template <class P, int W>
+int segsum_resident_warps()
+{
+    using SM = WarpSmem<P, W>;
+    constexpr int B = pick_bunches_per_block(SM::BYTES);
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (cache[dev] > 0) return cache[dev];
+    auto kb = segsum_kernel<P, W, B>;
+    int nb = 0;
+    if (cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, B * SM::BYTES) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kb, B * 32, B * SM::BYTES) !=
+            cudaSuccess ||
+        nb <= 0) {
+        (void)cudaGetLastError();
+        return B;  // at least one block
+    }
+    cache[dev] = nb * B;
+    return cache[dev];
+}
+
+// choose S (tiles per bunch) and the bunch count for this call
+template <class P, int W>
+void resolve_bunches(Layout &l, int32_t S_opt)
+{
+    if (l.ntiles == 0) {
+        l.S = S_opt > 0 ? S_opt : 1;
+        l.nbunches = 0;
+        return;
+    }
+    if (S_opt > 0) {
+        l.S = S_opt;
+    } else {
+        int64_t total = (int64_t)device_sm_count() * segsum_resident_warps<P, W>();
+        if (total > kMaxAutoBunches) total = kMaxAutoBunches;
+        if (total < 1) total = 1;
+        l.S = (int32_t)((l.ntiles + total - 1) / total);
+    }
+    l.nbunches = (l.ntiles + l.S - 1) / l.S;
+}
+
+template <class P, int W>
+int run_shape(const Call &c)
+{
+    using SM = WarpSmem<P, W>;
+    constexpr int B = pick_bunches_per_block(SM::BYTES);
+    const Layout &l = c.lay;
+    unsigned char *ws = c.ws;
+    uint32_t *err = reinterpret_cast<uint32_t *>(ws + l.off_err);
+    int32_t *toff = reinterpret_cast<int32_t *>(ws + l.off_tile_offset);
+    uint32_t *info = reinterpret_cast<uint32_t *>(ws + l.off_tile_info);
+    int32_t *sidx = reinterpret_cast<int32_t *>(ws + l.off_sync_idx);
+    void *sval = ws + l.off_sync_val;
+    void *tval = ws + l.off_tail_val;
+    int32_t *tflag = reinterpret_cast<int32_t *>(ws + l.off_tail_flag);
+    cudaError_t e;
+
+    if (c.ev) cudaEventRecord(c.ev[0], c.stream);
+    {
+        launch_partition(c.row_ptr, c.m, c.nnz, l.L, l.ntiles, toff, err, c.stream);
+    }
+    if (c.ev) cudaEventRecord(c.ev[1], c.stream);
+    if (l.ntiles > 0) {
+        SegsumArgs a;
+        a.row_ptr = c.row_ptr;
+        a.col = c.col;
+        a.val = c.val;
+        a.x = c.x;
+        a.y = c.y;
+        a.tile_offset = toff;
+        a.tile_info = info;
+        a.sync_idx = sidx;
+        a.sync_val = sval;
+        a.tail_val = tval;
+        a.tail_flag = tflag;
+        a.err = err;
+        a.dbg_desc = c.dbg_desc;
+        a.m = c.m;
+        a.nnz = c.nnz;
+        a.ntiles = l.ntiles;
+        a.nbunches = l.nbunches;
+        a.S = l.S;
+        auto kb = segsum_kernel<P, W, B>;
+        static int attr_done[64] = {0};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+            e = cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     B * SM::BYTES);
+            if (e != cudaSuccess) return record_cuda_error(e);
+            attr_done[dev] = 1;
+        }
+        const unsigned grid = (unsigned)((l.nbunches + B - 1) / B);
+        kb<<<grid, B * 32, B * SM::BYTES, c.stream>>>(a);
+    }
+    if (c.dbg_yspec && c.m > 0) {
+        e = cudaMemcpyAsync(c.dbg_yspec, c.y, sizeof(typename P::y_t) * (size_t)c.m,
+                            cudaMemcpyDeviceToDevice, c.stream);
+        if (e != cudaSuccess) return record_cuda_error(e);
+    }
+    if (c.ev) cudaEventRecord(c.ev[2], c.stream);
+    {
+        CalibArgs a;
+        a.row_ptr = c.row_ptr;
+        a.tile_offset = toff;
+        a.tile_info = info;
+        a.sync_idx = sidx;
+        a.sync_val = sval;
+        a.tail_val = tval;
+        a.tail_flag = tflag;
+        a.y = c.y;
+        a.err = err;
+        a.m = c.m;
+        a.nnz = c.nnz;
+        a.L = l.L;
+        a.ntiles = l.ntiles;
+        a.nbunches = l.nbunches;
+        a.nblk_tiles = (int32_t)((l.ntiles + kCalibWarps - 1) / kCalibWarps);
+        a.nblk_sync = (int32_t)((l.nbunches + kCalibWarps - 1) / kCalibWarps);
+        a.nblk_zero = kZeroBlocks;
+        const unsigned grid = (unsigned)(a.nblk_tiles + a.nblk_sync + a.nblk_zero);
+        calibrate_kernel<P><<<grid, kCalibWarps * 32, 0, c.stream>>>(a);
+    }
+    if (c.ev) cudaEventRecord(c.ev[3], c.stream);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return record_cuda_error(e);
+    return SSSPMV_OK;
+}
+
+}  // namespace ssspmv

@@ -1,0 +1,451 @@
+// segsum.cuh -- the three kernels of CSR SpMV by speculative segmented sum
+// (Liu & Vinter, Sec. 3 and Algorithm 1), written for sm_103a.
+//
+//   (a) partition_kernel   tile_offset[t] = max{r : row_ptr[r] <= b_t}
+//   (b) segsum_kernel      per tile: on-chip row-start descriptor from row_ptr,
+//                          x gathers, FMA accumulation per segment, transmitter
+//                          carried between the tiles of a bunch, speculative
+//                          stores y[tile_offset[t] + s], synchronizer records
+//   (c) calibrate_kernel   synchronizer sums, re-arrangement of dirty tiles,
+//                          zeroing of empty rows
+//
+// Tile t holds the nonzeros [b_t, b_{t+1}), b_t = min(t*L, nnz), L = 32*W.
+// A warp is the paper's thread-bunch and owns S consecutive tiles; lane l of
+// the warp owns the W consecutive entries [l*W, (l+1)*W) of each tile (the
+// W x T tile of Sec. 3.1).  W is odd, so lane-strided shared-memory reads of
+// a tile are free of bank conflicts without padding, and 32*W entries of 4 or
+// 8 bytes are still a multiple of 16 bytes for the bulk copies.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "layout.h"
+#include "ptx.cuh"
+
+namespace ssspmv {
+
+// ---------------------------------------------------------------------------
+// precision traits
+
+struct F64 {
+    using val_t = double;
+    using x_t = double;
+    using y_t = double;
+    using acc_t = double;
+    __device__ static __forceinline__ acc_t zero() { return 0.0; }
+    __device__ static __forceinline__ acc_t fma(val_t v, x_t x, acc_t a) { return __fma_rn(v, x, a); }
+    __device__ static __forceinline__ acc_t add(acc_t a, acc_t b) { return __dadd_rn(a, b); }
+    __device__ static __forceinline__ y_t out(acc_t a) { return a; }
+    __device__ static __forceinline__ x_t gather(const x_t *x, int32_t c, uint64_t pol)
+    {
+        return ldg_keep(x + c, pol);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// kernel (a): partition (Sec. 3.2: binary search of the tile boundaries on
+// row_ptr, returning the rightmost match).  One thread per boundary.
+
+// Thread 0 also clears the workspace's device error word for this call.
+void launch_partition(const int32_t *row_ptr, int32_t m, int32_t nnz, int32_t L, int64_t ntiles,
+                      int32_t *tile_offset, uint32_t *err, cudaStream_t stream);
+
+// ---------------------------------------------------------------------------
+// shared-memory layout of one warp in kernel (b)
+
+template <class P, int W>
+struct WarpSmem {
+    static constexpr int L = 32 * W;
+    static constexpr int VAL_BYTES = L * (int)sizeof(typename P::val_t);
+    static constexpr int COL_BYTES = L * 4;
+    static constexpr int VAL_REGION = (VAL_BYTES + 15) & ~15;
+    static constexpr int STAGE_BYTES = ((VAL_REGION + COL_BYTES) + 127) & ~127;
+    static constexpr int STAGES = 2;
+    static constexpr int BAR_OFF = STAGES * STAGE_BYTES;
+    static constexpr int DESC_OFF = BAR_OFF + STAGES * 8;
+    static constexpr int DESC_WORDS = W + 1;  // one spare word for 64-bit windows
+    static constexpr int SLOT_OFF = (DESC_OFF + DESC_WORDS * 4 + 15) & ~15;
+    static constexpr int BYTES = (SLOT_OFF + 32 + 127) & ~127;
+};
+
+// warps per block maximising resident warps per SM for a given per-warp
+// shared-memory footprint (228 KB per SM, 227 KB per block, 1 KB reserved
+// per block)
+constexpr int pick_bunches_per_block(int warp_bytes)
+{
+    int best_b = 1, best_w = 0;
+    for (int b = 1; b <= 32; ++b) {
+        long blk = (long)b * warp_bytes;
+        if (blk > 232448) break;
+        int per_sm = (int)(233472 / (blk + 1024));
+        if (per_sm > 32 / b + 1) per_sm = 32 / b + 1;
+        int w = per_sm * b;
+        if (w >= best_w) { best_w = w; best_b = b; }
+    }
+    return best_b;
+}
+
+struct SegsumArgs {
+    const int32_t *row_ptr;
+    const int32_t *col;
+    const void *val;
+    const void *x;
+    void *y;
+    const int32_t *tile_offset;
+    uint32_t *tile_info;
+    int32_t *sync_idx;
+    void *sync_val;
+    void *tail_val;
+    int32_t *tail_flag;
+    uint32_t *err;
+    uint32_t *dbg_desc;  // nullable
+    int32_t m;
+    int32_t nnz;
+    int64_t ntiles;
+    int64_t nbunches;
+    int32_t S;
+};
+
+// ---------------------------------------------------------------------------
+// kernel (b): one warp = one thread-bunch over S consecutive tiles
+
+template <class P, int W, int B>
+__global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
+{
+    using V = typename P::val_t;
+    using X = typename P::x_t;
+    using Y = typename P::y_t;
+    using A = typename P::acc_t;
+    using SM = WarpSmem<P, W>;
+    constexpr int L = SM::L;
+    constexpr int STAGES = SM::STAGES;
+    static_assert(W % 2 == 1 && W <= 31, "W must be odd and at most 31");
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    unsigned char *base = smem_raw + warp * SM::BYTES;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + SM::BAR_OFF);
+    uint32_t *desc = reinterpret_cast<uint32_t *>(base + SM::DESC_OFF);
+    A *slot_f = reinterpret_cast<A *>(base + SM::SLOT_OFF);       // bunch-first partial
+    A *slot_carry = reinterpret_cast<A *>(base + SM::SLOT_OFF + 16);  // transmitter
+
+    const int64_t w = (int64_t)blockIdx.x * B + warp;
+    if (w >= a.nbunches) return;
+    const int64_t t0 = w * a.S;
+    const int64_t t1 = (t0 + a.S < a.ntiles) ? t0 + a.S : a.ntiles;
+    if (t0 >= t1) return;
+
+    const V *__restrict__ val = static_cast<const V *>(a.val);
+    const X *__restrict__ x = static_cast<const X *>(a.x);
+    Y *__restrict__ y = static_cast<Y *>(a.y);
+    const int32_t *__restrict__ row_ptr = a.row_ptr;
+    const int32_t *__restrict__ col = a.col;
+    const int32_t nnz = a.nnz;
+
+    const uint64_t pol_stream = policy_evict_first();
+    const uint64_t pol_keep = policy_evict_last();
+
+    auto stage_ptr = [&](int s) { return base + s * SM::STAGE_BYTES; };
+    // issue the bulk copies of tile tt into stage s (lane 0 only)
+    auto issue = [&](int64_t tt, int s) {
+        const int64_t b = tt * L;
+        const int32_t len = (int32_t)((nnz - b < L) ? nnz - b : L);
+        const uint32_t vb = ((uint32_t)len * (uint32_t)sizeof(V)) & ~15u;
+        const uint32_t cb = ((uint32_t)len * 4u) & ~15u;
+        mbar_arrive_expect_tx(&bar[s], vb + cb);
+        if (vb) bulk_g2s(stage_ptr(s), val + b, vb, &bar[s], pol_stream);
+        if (cb) bulk_g2s(stage_ptr(s) + SM::VAL_REGION, col + b, cb, &bar[s], pol_stream);
+    };
+
+    if (lane == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (lane == 0) {
+        for (int s = 0; s < STAGES && t0 + s < t1; ++s) issue(t0 + s, s);
+    }
+
+    const int32_t rF = __ldg(a.tile_offset + t0);  // the bunch's first row
+    int32_t start = rF;
+    A carry = P::zero();
+    A F = P::zero(), G = P::zero();
+    bool hasG = false;
+
+    for (int64_t t = t0; t < t1; ++t) {
+        const int it = (int)(t - t0);
+        const int s = it % STAGES;
+        const uint32_t par = (uint32_t)((it / STAGES) & 1);
+        const int64_t b = t * L;
+        const int32_t len = (int32_t)((nnz - b < L) ? nnz - b : L);
+        const int64_t e = b + len;
+        const int32_t stop = __ldg(a.tile_offset + t + 1);
+
+        // ---- segment descriptor built on chip from row_ptr[start..stop]
+        // (Sec. 3.2: offsets of the covered row pointers from the boundary;
+        // every row start inside the tile, including row `stop`'s) and the
+        // empty-row ("dirty") test over [start, stop).
+        if (lane <= W) desc[lane] = 0u;
+        __syncwarp();
+        bool dirty = false, cont = false, raw0 = false;
+        for (int64_t r0 = start; r0 <= stop; r0 += 32) {
+            const int32_t r = (int32_t)(r0 + lane);
+            if (r0 + lane <= stop) {
+                const int32_t pr = __ldg(row_ptr + r);
+                const int64_t k = (int64_t)pr - b;
+                if (k >= 0 && k < len) atomicOr(&desc[k >> 5], 1u << (k & 31));
+                if (r < stop && __ldg(row_ptr + r + 1) == pr) dirty = true;
+                if (r == start && k == 0) raw0 = true;
+                if (r == stop && (int64_t)pr < e) cont = true;
+            }
+        }
+        dirty = __any_sync(FULL, dirty);
+        cont = __any_sync(FULL, cont);
+        raw0 = __any_sync(FULL, raw0);
+        __syncwarp();
+        const int bit0 = lane * W;
+        const uint64_t win =
+            ((uint64_t)desc[(bit0 >> 5) + 1] << 32) | (uint64_t)desc[bit0 >> 5];
+        uint32_t hb = (uint32_t)(win >> (bit0 & 31)) & ((1u << W) - 1u);
+        if (a.dbg_desc != nullptr && lane < W) a.dbg_desc[t * W + lane] = desc[lane];
+        if (lane == 0) hb |= 1u;  // each tile opens with a segment (Sec. 3.2)
+
+        // ---- wait for this tile's val/col
+        unsigned char *st = stage_ptr(s);
+        const V *vs = reinterpret_cast<const V *>(st);
+        const int32_t *cs = reinterpret_cast<const int32_t *>(st + SM::VAL_REGION);
+        if (!mbar_wait_bounded(&bar[s], par)) {
+            if (lane == 0) atomicOr(a.err, SSSPMV_DEV_TIMEOUT);
+            // drain the copies still in flight before leaving
+            for (int64_t tt = t; tt < t + STAGES && tt < t1; ++tt) {
+                const int jt = (int)(tt - t0);
+                mbar_wait_bounded(&bar[jt % STAGES], (uint32_t)((jt / STAGES) & 1));
+            }
+            return;
+        }
+        if (len < L) {  // ragged last tile: the bulk copies stop at 16-byte multiples
+            V *vw = reinterpret_cast<V *>(st);
+            int32_t *cw = reinterpret_cast<int32_t *>(st + SM::VAL_REGION);
+            const int32_t vdone = (int32_t)((((uint32_t)len * (uint32_t)sizeof(V)) & ~15u) / sizeof(V));
+            const int32_t cdone = (int32_t)((((uint32_t)len * 4u) & ~15u) / 4u);
+            for (int32_t k = vdone + lane; k < len; k += 32) vw[k] = val[b + k];
+            for (int32_t k = cdone + lane; k < len; k += 32) cw[k] = col[b + k];
+            __syncwarp();
+        }
+
+        // ---- gathers of x for the lane's W entries (Alg. 1 products)
+        X xv[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const int k = lane * W + j;
+            xv[j] = (k < len) ? P::gather(x, cs[k], pol_keep) : X(0);
+        }
+
+        // ---- compact indices: exclusive scan of head counts (Alg. 1 y_index)
+        const int c = __popc(hb);
+        const int incl = warp_inclusive_scan(c, lane);
+        const int idx0 = incl - c;
+        const int nseg = __shfl_sync(FULL, incl, 31);
+        const A cin = (raw0 || t == t0) ? P::zero() : carry;  // transmitter
+
+        auto emit = [&](int sidx, A v) {
+            if (sidx == 0 && start == rF) {
+                *slot_f = v;
+            } else {
+                const int64_t row = (int64_t)start + sidx;
+                if (row < a.m) y[row] = P::out(v);
+                else atomicOr(a.err, SSSPMV_DEV_RANGE);
+            }
+        };
+
+        // ---- per-lane sequential segmented sum: one FMA per entry; a head
+        // closes the open segment (the part before the lane's first head
+        // belongs to a segment opened in an earlier lane)
+        A acc = P::zero(), pre = P::zero();
+        int cur = idx0 - 1;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const int k = lane * W + j;
+            if ((hb >> j) & 1u) {
+                if (cur >= idx0) emit(cur, acc);
+                else pre = acc;
+                ++cur;
+                acc = (j == 0 && lane == 0) ? cin : P::zero();
+            }
+            if (k < len) acc = P::fma(vs[k], xv[j], acc);
+        }
+        const bool has = c > 0;
+        if (!has) pre = acc;
+        const A v = acc;  // suffix (open segment) if has, else the lane total
+
+        // ---- cross-lane segmented sum of the open segments:
+        // C_l = sum of v over lanes first_l..l, first_l = last lane <= l with
+        // a head.  Short chains are summed serially, long ones by a scan.
+        const unsigned hm = __ballot_sync(FULL, has);
+        const unsigned le = hm & ((lane == 31) ? FULL : ((2u << lane) - 1u));
+        const int first = 31 - __clz(le);
+        const int span = __reduce_max_sync(FULL, (unsigned)(lane - first));
+        A C = v;
+        if (span <= 4) {
+            for (int d = 1; d <= span; ++d) {
+                const A o = __shfl_up_sync(FULL, v, d);
+                if (lane - d >= first) C = P::add(C, o);
+            }
+        } else {
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const A o = __shfl_up_sync(FULL, C, d);
+                if (lane - d >= first) C = P::add(C, o);
+            }
+        }
+        const A Cprev = __shfl_up_sync(FULL, C, 1);
+        // a lane with a head closes the segment left open before it
+        if (has && lane > 0) emit(idx0 - 1, P::add(Cprev, pre));
+        // the tile's last segment: stored, or carried if row `stop` goes on
+        if (lane == 31) {
+            *slot_carry = C;
+            if (nseg == 1 && start == rF) {
+                *slot_f = C;          // still the bunch's first segment
+            } else if (cont) {
+                if (t == t1 - 1) {    // continues into the next bunch
+                    G = C;
+                    hasG = true;
+                }                     // else the next tile of this bunch stores it
+            } else {
+                emit(nseg - 1, C);
+            }
+        }
+        if (lane == 0) a.tile_info[t] = (uint32_t)nseg | (dirty ? 0x80000000u : 0u);
+        __syncwarp();
+        carry = *slot_carry;
+        // ---- release the stage: copy the tile S+STAGES ahead into it
+        if (lane == 0 && t + STAGES < t1) {
+            fence_proxy_async_smem();
+            issue(t + STAGES, s);
+        }
+        start = stop;
+    }
+    __syncwarp();
+    F = *slot_f;
+    G = __shfl_sync(FULL, G, 31);
+    hasG = __shfl_sync(FULL, hasG, 31);
+    if (lane == 0) {
+        a.sync_idx[w] = rF;
+        static_cast<A *>(a.sync_val)[w] = F;
+        static_cast<A *>(a.tail_val)[w] = hasG ? G : P::zero();
+        a.tail_flag[w] = hasG ? 1 : 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// kernel (c): calibration.  Block roles by blockIdx.x:
+//   [0, nblk_tiles)                 one warp per tile: re-arrange dirty tiles
+//   [nblk_tiles, +nblk_sync)        one warp per bunch: synchronizer sums
+//   [..., +nblk_zero)               grid-stride zeroing of leading empty rows
+
+struct CalibArgs {
+    const int32_t *row_ptr;
+    const int32_t *tile_offset;
+    const uint32_t *tile_info;
+    const int32_t *sync_idx;
+    const void *sync_val;
+    const void *tail_val;
+    const int32_t *tail_flag;
+    void *y;
+    uint32_t *err;
+    int32_t m;
+    int32_t nnz;
+    int32_t L;
+    int64_t ntiles;
+    int64_t nbunches;
+    int32_t nblk_tiles;
+    int32_t nblk_sync;
+    int32_t nblk_zero;
+};
+
+constexpr int kCalibWarps = 8;
+
+template <class P>
+__global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const CalibArgs a)
+{
+    using Y = typename P::y_t;
+    using A = typename P::acc_t;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    Y *__restrict__ y = static_cast<Y *>(a.y);
+    const int32_t *__restrict__ row_ptr = a.row_ptr;
+    int blk = blockIdx.x;
+
+    if (blk < a.nblk_tiles) {
+        // ---- re-arrangement of a dirty tile (Sec. 3.2, checking prediction)
+        const int64_t t = (int64_t)blk * kCalibWarps + warp;
+        if (t >= a.ntiles) return;
+        const uint32_t info = __ldg(a.tile_info + t);
+        if (!(info >> 31)) return;
+        const int32_t nseg = (int32_t)(info & 0x7fffffffu);
+        const int32_t start = __ldg(a.tile_offset + t);
+        const int32_t stop = __ldg(a.tile_offset + t + 1);
+        const int64_t e = (t + 1) * (int64_t)a.L < a.nnz ? (t + 1) * (int64_t)a.L : a.nnz;
+        const bool cont = stop < a.m && (int64_t)__ldg(row_ptr + stop) < e;
+        // non-empty rows strictly inside (start, stop): each holds one segment
+        const int32_t K = nseg - 1 - (cont ? 1 : 0);
+        int32_t above = 0;
+        // walk down from stop-1 so that every slot is read before any write
+        // can reach it (the s-th partial moves from start+s up to its row)
+        for (int32_t hi = stop - 1; hi > start; hi -= 32) {
+            const int32_t r = hi - lane;
+            const bool valid = r > start;
+            const bool ne = valid && __ldg(row_ptr + r + 1) > __ldg(row_ptr + r);
+            const unsigned mask = __ballot_sync(FULL, ne);
+            const int32_t q = above + __popc(mask & ((1u << lane) - 1u));
+            Y v = Y(0);
+            if (ne) {
+                const int32_t sidx = K - q;
+                if (sidx >= 1 && sidx <= K) v = y[start + sidx];
+                else atomicOr(a.err, SSSPMV_DEV_CALIB);
+            }
+            __syncwarp();
+            if (valid) y[r] = ne ? v : Y(0);
+            above += __popc(mask);
+            __syncwarp();
+        }
+        if (lane == 0 && above != K) atomicOr(a.err, SSSPMV_DEV_CALIB);
+        return;
+    }
+    blk -= a.nblk_tiles;
+    if (blk < a.nblk_sync) {
+        // ---- synchronization (Alg. 1 synchronization step, on the GPU): the
+        // run of bunches sharing a first row adds into that row, plus the
+        // tail partial the previous bunch left for it
+        const int64_t w = (int64_t)blk * kCalibWarps + warp;
+        if (w >= a.nbunches) return;
+        const int32_t r = __ldg(a.sync_idx + w);
+        if (w > 0 && __ldg(a.sync_idx + w - 1) == r) return;
+        const A *sv = static_cast<const A *>(a.sync_val);
+        double acc = 0.0;  // calibration sums are kept in FP64
+        for (int64_t base = w;; base += 32) {
+            const int64_t ww = base + lane;
+            const bool in = ww < a.nbunches && __ldg(a.sync_idx + ww) == r;
+            if (in) acc += (double)sv[ww];
+            if (__popc(__ballot_sync(FULL, in)) < 32) break;
+        }
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) acc += __shfl_xor_sync(FULL, acc, d);
+        if (lane == 0) {
+            if (w > 0 && __ldg(a.tail_flag + w - 1))
+                acc += (double)static_cast<const A *>(a.tail_val)[w - 1];
+            if (r >= 0 && r < a.m) y[r] = (Y)acc;
+            else atomicOr(a.err, SSSPMV_DEV_RANGE);
+        }
+        return;
+    }
+    blk -= a.nblk_sync;
+    // ---- rows before tile_offset[0] are empty and covered by no tile
+    const int32_t r0 = __ldg(a.tile_offset);
+    for (int64_t r = (int64_t)blk * blockDim.x + threadIdx.x; r < r0;
+         r += (int64_t)a.nblk_zero * blockDim.x)
+        y[r] = Y(0);
+}
+
+}  // namespace ssspmv

@@ -1,0 +1,211 @@
+"""ctypes binding of libssspmv.so (include/ssspmv.h): the same entry points
+under the same names, with argument marshalling only.  Every step of the
+product runs in the library's CUDA kernels; there is no Python or CPU
+fallback, and loading fails loudly when the library has not been built.
+
+Array arguments may be torch tensors (device memory, contiguous) or raw
+integer addresses.  Streams may be torch.cuda.Stream objects, raw handles or
+None (the current torch stream when torch is importable, else the legacy
+default stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libssspmv.so")
+HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "ssspmv.h")
+
+SSSPMV_OK = 0
+SSSPMV_EINVAL = -1
+SSSPMV_EWORKSPACE = -2
+SSSPMV_ECUDA = -3
+SSSPMV_EDEVICE = -4
+SSSPMV_EUNSUPPORTED = -5
+
+
+class SsspmvError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = _lib().ssspmv_strerror(code).decode()
+        if code == SSSPMV_ECUDA:
+            msg += " (cudaError %d)" % _lib().ssspmv_last_cuda_error()
+        super().__init__("%s: %s (%d)" % (where, msg, code))
+
+
+class ssspmv_opts(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_int32), ("S", ctypes.c_int32), ("validate", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("stage_events", ctypes.c_void_p)]
+
+
+_L = None
+P = ctypes.c_void_p
+i32, i64, u32, sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_size_t
+OPTS = ctypes.POINTER(ssspmv_opts)
+
+_SIGS = {
+    "ssspmv_plan_shape": (ctypes.c_int, [i32, i32, i32, OPTS, P, P, P, P, P]),
+    "ssspmv_workspace_bytes": (sz, [i32, i32, i32, OPTS]),
+    "ssspmv_csr_f64": (ctypes.c_int, [i32, i32, i32, P, P, P, P, P, OPTS, P, sz, P]),
+    "ssspmv_host_buffer_bytes": (sz, [i32, i32, i32, OPTS]),
+    "ssspmv_csr_f64_host": (ctypes.c_int, [i32, i32, i32, P, P, P, P, P, OPTS, P, sz, P]),
+    "ssspmv_csr_f64_debug": (ctypes.c_int, [i32, i32, i32, P, P, P, P, P, OPTS, P, sz, P,
+                                            P, P, P, P, P]),
+    "ssspmv_validate_csr": (ctypes.c_int, [i32, i32, i32, P, P, P, P]),
+    "ssspmv_device_status": (ctypes.c_int, [P, sz, P, ctypes.c_int, P]),
+    "ssspmv_supported_w": (ctypes.c_int, [P, i32, P]),
+    "ssspmv_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "ssspmv_last_cuda_error": (ctypes.c_int, []),
+    "ssspmv_version": (ctypes.c_int, []),
+}
+
+
+def _lib():
+    global _L
+    if _L is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libssspmv.so is not built (run __graft_entry__.build() or "
+                              "python -m paper_1504_06474_gb300._build)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _L = lib
+    return _L
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/ssspmv.h declares."""
+    with open(HEADER_PATH) as f:
+        text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    return sorted(set(re.findall(r"\b(ssspmv_[a-z0-9_]+)\s*\(", text)))
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        if a.numel() and not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr() if a.numel() else None
+    if hasattr(a, "ctypes"):  # numpy array (host)
+        return a.ctypes.data if a.size else None
+    raise TypeError("cannot take the address of %r" % type(a))
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def make_opts(W: int = 0, S: int = 0, stage_events=None) -> ssspmv_opts:
+    o = ssspmv_opts()
+    o.W, o.S, o.validate, o.reserved = W, S, 0, 0
+    o.stage_events = stage_events
+    return o
+
+
+def _opts(o):
+    return None if o is None else ctypes.byref(o)
+
+
+def check(rc: int, where: str):
+    if rc != SSSPMV_OK:
+        raise SsspmvError(rc, where)
+
+
+# --- entry points (same names as the C ABI) --------------------------------
+
+def ssspmv_plan_shape(m, nnz, val_bytes=8, opts=None):
+    W, L, S = i32(), i32(), i32()
+    nt, nb = i64(), i64()
+    rc = _lib().ssspmv_plan_shape(m, nnz, val_bytes, _opts(opts), ctypes.byref(W),
+                                  ctypes.byref(L), ctypes.byref(S), ctypes.byref(nt),
+                                  ctypes.byref(nb))
+    check(rc, "ssspmv_plan_shape")
+    return dict(W=W.value, L=L.value, S=S.value, ntiles=nt.value, nbunches=nb.value)
+
+
+def ssspmv_workspace_bytes(m, nnz, val_bytes=8, opts=None) -> int:
+    return int(_lib().ssspmv_workspace_bytes(m, nnz, val_bytes, _opts(opts)))
+
+
+def ssspmv_csr_f64(m, n, nnz, row_ptr, col_idx, val, x, y, opts=None, workspace=None,
+                   ws_bytes=None, stream=None) -> int:
+    if ws_bytes is None:
+        ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    return _lib().ssspmv_csr_f64(m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(val), _ptr(x),
+                                 _ptr(y), _opts(opts), _ptr(workspace), ws_bytes,
+                                 _stream(stream))
+
+
+def ssspmv_host_buffer_bytes(m, n, nnz, opts=None) -> int:
+    return int(_lib().ssspmv_host_buffer_bytes(m, n, nnz, _opts(opts)))
+
+
+def ssspmv_csr_f64_host(m, n, nnz, host_row_ptr, host_col_idx, host_val, host_x, host_y,
+                        opts=None, dev_buffer=None, dev_bytes=None, stream=None) -> int:
+    if dev_bytes is None:
+        dev_bytes = dev_buffer.numel() * dev_buffer.element_size() if dev_buffer is not None else 0
+    return _lib().ssspmv_csr_f64_host(m, n, nnz, _ptr(host_row_ptr), _ptr(host_col_idx),
+                                      _ptr(host_val), _ptr(host_x), _ptr(host_y), _opts(opts),
+                                      _ptr(dev_buffer), dev_bytes, _stream(stream))
+
+
+def ssspmv_csr_f64_debug(m, n, nnz, row_ptr, col_idx, val, x, y, opts=None, workspace=None,
+                         ws_bytes=None, stream=None, tile_offset=None, desc=None,
+                         tile_info=None, sync_idx=None, y_spec=None) -> int:
+    if ws_bytes is None:
+        ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    return _lib().ssspmv_csr_f64_debug(m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(val),
+                                       _ptr(x), _ptr(y), _opts(opts), _ptr(workspace), ws_bytes,
+                                       _stream(stream), _ptr(tile_offset), _ptr(desc),
+                                       _ptr(tile_info), _ptr(sync_idx), _ptr(y_spec))
+
+
+def ssspmv_validate_csr(m, n, nnz, row_ptr, col_idx, scratch, stream=None) -> int:
+    return _lib().ssspmv_validate_csr(m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(scratch),
+                                      _stream(stream))
+
+
+def ssspmv_device_status(workspace, ws_bytes=None, stream=None, clear=False) -> int:
+    if ws_bytes is None:
+        ws_bytes = workspace.numel() * workspace.element_size()
+    bits = u32()
+    rc = _lib().ssspmv_device_status(_ptr(workspace), ws_bytes, _stream(stream), int(clear),
+                                     ctypes.byref(bits))
+    check(rc, "ssspmv_device_status")
+    return bits.value
+
+
+def ssspmv_supported_w() -> list[int]:
+    buf = (i32 * 16)()
+    cnt = i32()
+    _lib().ssspmv_supported_w(buf, 16, ctypes.byref(cnt))
+    return [buf[i] for i in range(min(cnt.value, 16))]
+
+
+def ssspmv_strerror(code: int) -> str:
+    return _lib().ssspmv_strerror(code).decode()
+
+
+def ssspmv_last_cuda_error() -> int:
+    return _lib().ssspmv_last_cuda_error()
+
+
+def ssspmv_version() -> int:
+    return _lib().ssspmv_version()

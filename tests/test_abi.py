@@ -1,0 +1,105 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function the
+header declares; host-side argument checks reject bad calls without touching a
+GPU.  No kernel is launched here."""
+import ctypes
+import shutil
+
+import pytest
+
+from paper_1504_06474_gb300 import _build
+from paper_1504_06474_gb300 import ssspmv as S
+
+pytestmark = pytest.mark.skipif(shutil.which("nvcc") is None and not
+                                __import__("os").path.exists("/usr/local/cuda/bin/nvcc"),
+                                reason="nvcc not available")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return S._lib()
+
+
+def test_exports_every_declared_function(lib):
+    names = S.declared_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding wraps each of them under the same name
+    for n in names:
+        assert callable(getattr(S, n)), n
+
+
+def test_host_only_queries(lib):
+    assert S.ssspmv_version() >= 10000
+    assert S.ssspmv_strerror(S.SSSPMV_EINVAL) == "invalid argument"
+    ws = S.ssspmv_supported_w()
+    assert ws and all(w % 2 == 1 and w <= 31 for w in ws)
+    # workspace size does not depend on a device
+    a = S.ssspmv_workspace_bytes(4_096_000, 109_215_352, 8, None)
+    b = S.ssspmv_workspace_bytes(4_096_000, 109_215_352, 8, S.make_opts(W=27))
+    assert a > 0 and b > 0 and a % 256 == 0
+    assert S.ssspmv_workspace_bytes(-1, 0, 8, None) == 0
+    assert S.ssspmv_workspace_bytes(10, 10, 8, S.make_opts(W=4)) == 0  # even W not compiled
+    assert S.ssspmv_workspace_bytes(10, 10, 3, None) == 0
+
+
+FAKE = 0x7f0000000000  # never dereferenced: every call below fails on the host
+
+
+@pytest.mark.parametrize("args,code", [
+    ((-1, 4, 0), S.SSSPMV_EINVAL),
+    ((4, -1, 0), S.SSSPMV_EINVAL),
+    ((0, 4, 3), S.SSSPMV_EINVAL),
+])
+def test_bad_scalars(lib, args, code):
+    m, n, nnz = args
+    rc = S.ssspmv_csr_f64(m, n, nnz, FAKE, FAKE, FAKE, FAKE, FAKE, workspace=FAKE, ws_bytes=1 << 30)
+    assert rc == code
+
+
+def test_null_and_misaligned(lib):
+    rc = S.ssspmv_csr_f64(4, 4, 8, None, FAKE, FAKE, FAKE, FAKE, workspace=FAKE, ws_bytes=1 << 30)
+    assert rc == S.SSSPMV_EINVAL
+    rc = S.ssspmv_csr_f64(4, 4, 8, FAKE, FAKE + 4, FAKE, FAKE, FAKE, workspace=FAKE,
+                          ws_bytes=1 << 30)
+    assert rc == S.SSSPMV_EINVAL          # col_idx not 16-byte aligned
+    rc = S.ssspmv_csr_f64(4, 4, 8, FAKE, FAKE, FAKE + 8, FAKE, FAKE, workspace=FAKE,
+                          ws_bytes=1 << 30)
+    assert rc == S.SSSPMV_EINVAL          # val not 16-byte aligned
+    rc = S.ssspmv_csr_f64(4, 0, 8, FAKE, FAKE, FAKE, FAKE, FAKE, workspace=FAKE, ws_bytes=1 << 30)
+    assert rc == S.SSSPMV_EINVAL          # entries but no columns
+
+
+def test_workspace_checks(lib):
+    need = S.ssspmv_workspace_bytes(100, 1000, 8, None)
+    rc = S.ssspmv_csr_f64(100, 100, 1000, FAKE, FAKE, FAKE, FAKE, FAKE, workspace=None,
+                          ws_bytes=need)
+    assert rc == S.SSSPMV_EWORKSPACE
+    rc = S.ssspmv_csr_f64(100, 100, 1000, FAKE, FAKE, FAKE, FAKE, FAKE, workspace=FAKE,
+                          ws_bytes=need - 1)
+    assert rc == S.SSSPMV_EWORKSPACE
+    rc = S.ssspmv_csr_f64(100, 100, 1000, FAKE, FAKE, FAKE, FAKE, FAKE, workspace=FAKE + 16,
+                          ws_bytes=need)
+    assert rc == S.SSSPMV_EWORKSPACE      # workspace must be 256-byte aligned
+
+
+def test_bad_opts(lib):
+    o = S.make_opts(S=-3)
+    rc = S.ssspmv_csr_f64(4, 4, 8, FAKE, FAKE, FAKE, FAKE, FAKE, opts=o, workspace=FAKE,
+                          ws_bytes=1 << 30)
+    assert rc == S.SSSPMV_EINVAL
+    o = S.make_opts(W=16)
+    rc = S.ssspmv_csr_f64(4, 4, 8, FAKE, FAKE, FAKE, FAKE, FAKE, opts=o, workspace=FAKE,
+                          ws_bytes=1 << 30)
+    assert rc == S.SSSPMV_EUNSUPPORTED
+
+
+def test_empty_matrix_is_a_noop(lib):
+    # m == 0: nothing to write, nothing launched
+    assert S.ssspmv_csr_f64(0, 5, 0, None, None, None, None, None) == S.SSSPMV_OK
+
+
+def test_opts_struct_layout(lib):
+    assert ctypes.sizeof(S.ssspmv_opts) == 24
+    assert S.ssspmv_opts.stage_events.offset == 16

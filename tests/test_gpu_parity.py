@@ -1,0 +1,224 @@
+"""Parity of the CUDA path with the CPU oracle, through the C ABI.
+
+Floating point: every row satisfies |y_i - yref_i| <= 1e-13 * s_i with yref
+the oracle's compensated (Dot2) row sum and s_i = sum_k |a_ik x_k|; rows with
+s_i = 0 must be exactly 0.  Integer artefacts (tile offsets, raw segment
+descriptors, dirty flags, segment counts, synchronizer rows) must match the
+oracle's independent derivations bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-13
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1504_06474_gb300 import _build
+    _build.build()
+    return torch.device("cuda:0")
+
+
+def _api():
+    from paper_1504_06474_gb300 import api, ssspmv
+    return api, ssspmv
+
+
+def check_case(dev, row_ptr, col, val, x, n, W=0, S=0, expect_exact=None):
+    api, C = _api()
+    A = api.to_device(row_ptr, col, val, n, dev)
+    xd = torch.as_tensor(x, dtype=torch.float64, device=dev)
+    opts = C.make_opts(W=W, S=S)
+    out = api.spmv_f64_debug(A, xd, opts)
+    shape = out["shape"]
+    L = shape["L"]
+    yref, s = oracle.spmv_dot2(row_ptr, col, val, x)
+    y = out["y"]
+    bad = np.nonzero(~(np.abs(y - yref) <= TOL * s))[0]
+    assert bad.size == 0, "rows %s: y=%s ref=%s s=%s (shape %s)" % (
+        bad[:5], y[bad[:5]], yref[bad[:5]], s[bad[:5]], shape)
+    assert np.all(y[s == 0] == 0.0)
+    if expect_exact is not None:
+        assert np.array_equal(y, expect_exact)
+    # index artefacts, bit for bit
+    toff = oracle.tile_offsets(row_ptr, L)
+    assert np.array_equal(out["tile_offset"], toff)
+    nt = shape["ntiles"]
+    if nt:
+        d = oracle.descriptors(row_ptr, L, toff)
+        assert np.array_equal(out["desc"], d)
+        dirty, nseg = oracle.tile_flags(row_ptr, L, toff)
+        info = out["tile_info"]
+        assert np.array_equal((info >> 31).astype(np.uint8), dirty)
+        assert np.array_equal((info & 0x7FFFFFFF).astype(np.int32), nseg)
+        Sx = shape["S"]
+        assert np.array_equal(out["sync_idx"], toff[np.arange(shape["nbunches"]) * Sx])
+    return out
+
+
+def test_paper_example_6x6(dev):
+    rp = np.array([0, 3, 6, 8, 8, 9, 12], np.int32)
+    col = np.array([0, 2, 5, 0, 1, 2, 2, 4, 4, 2, 3, 4], np.int32)
+    val = np.arange(3.0, 15.0)
+    x = np.arange(1.0, 7.0)
+    want = oracle.spmv(rp, col, val, x)
+    for W in _api()[1].ssspmv_supported_w():
+        check_case(dev, rp, col, val, x, 6, W=W, expect_exact=want)
+
+
+def test_uniform4096_all_shapes(dev):
+    A, x = synth.workload("uniform4096")
+    for W in _api()[1].ssspmv_supported_w():
+        for S in (0, 1, 2, 7):
+            check_case(dev, A.row_ptr, A.col, A.val, x, A.n, W=W, S=S)
+
+
+@pytest.mark.parametrize("seed,mean,p_empty,p_long,long_len", [
+    (1, 8, 0.5, 0.0, 0),        # half the rows empty: nearly every tile dirty
+    (2, 3, 0.2, 0.0, 0),        # short rows: many segments per lane
+    (3, 30, 0.05, 0.003, 20000),  # rows spanning many tiles and bunches
+    (4, 1, 0.0, 0.0, 0),        # mostly single-entry rows
+    (5, 60, 0.0, 0.0, 0),       # rows longer than a lane's run
+])
+def test_random_structures(dev, seed, mean, p_empty, p_long, long_len):
+    lens = synth.random_lengths(20000, seed=seed, mean=mean, p_empty=p_empty, p_long=p_long,
+                                long_len=long_len)
+    A = synth.from_lengths(lens, 5000, seed=seed)
+    x = synth.sym_vector(5000, seed=100 + seed)
+    for W in (15, 27):
+        for S in (0, 1, 3):
+            check_case(dev, A.row_ptr, A.col, A.val, x, A.n, W=W, S=S)
+
+
+@pytest.mark.parametrize("lens", [
+    [0] * 1000 + [5] * 10 + [0] * 7,            # leading and trailing empty rows
+    [100_000],                                  # one long row, many tiles
+    [0, 0, 0],                                  # nnz = 0: y must be zeroed
+    [1, 0, 2],                                  # fewer than 4 entries
+    [3] * 7,                                    # 21 entries: ragged single tile
+    [1] * 4000,                                 # a segment per entry
+    [27] * 1000 + [0] + [27] * 1000,            # lanes aligned with rows, one empty
+    [961, 0, 0, 961, 1],                        # rows exactly one tile long (W=31)
+    [0] * 5 + [405] * 3 + [0] * 2 + [405],      # rows aligned with 15-wide tiles
+])
+def test_edge_structures(dev, lens):
+    A = synth.from_lengths(lens, 64, seed=len(lens))
+    x = synth.sym_vector(64, seed=9)
+    for W in _api()[1].ssspmv_supported_w():
+        for S in (0, 1, 2):
+            check_case(dev, A.row_ptr, A.col, A.val, x, A.n, W=W, S=S)
+
+
+def test_duplicates_and_unsorted_columns(dev):
+    rng = np.random.Generator(np.random.PCG64(5))
+    lens = rng.integers(0, 40, size=3000)
+    rp = np.zeros(3001, np.int32)
+    np.cumsum(lens, out=rp[1:])
+    nnz = int(rp[-1])
+    col = rng.integers(0, 50, size=nnz).astype(np.int32)    # unsorted, repeated
+    val = rng.uniform(-1, 1, nnz)
+    x = rng.uniform(-1, 1, 50)
+    check_case(dev, rp, col, val, x, 50)
+
+
+def test_small_integers_exact(dev):
+    rng = np.random.Generator(np.random.PCG64(8))
+    lens = rng.integers(0, 70, size=5000)
+    rp = np.zeros(5001, np.int32)
+    np.cumsum(lens, out=rp[1:])
+    nnz = int(rp[-1])
+    col = rng.integers(0, 300, size=nnz).astype(np.int32)
+    val = rng.integers(-8, 9, size=nnz).astype(float)
+    x = rng.integers(-8, 9, size=300).astype(float)
+    want = oracle.spmv(rp, col, val, x)   # exact: every partial sum is an integer < 2^53
+    for W in _api()[1].ssspmv_supported_w():
+        check_case(dev, rp, col, val, x, 300, W=W, S=1, expect_exact=want)
+
+
+def test_nan_propagates_to_exactly_the_rows_that_use_it(dev):
+    A, x = synth.workload("uniform4096")
+    x = x.copy()
+    x[123] = np.nan
+    api, C = _api()
+    Ad = api.to_device(A.row_ptr, A.col, A.val, A.n, dev)
+    y = api.spmv_f64(Ad, torch.as_tensor(x, device=dev)).cpu().numpy()
+    uses = np.zeros(A.m, bool)
+    rows = np.repeat(np.arange(A.m), np.diff(A.row_ptr))
+    uses[rows[A.col == 123]] = True
+    assert np.array_equal(np.isnan(y), uses)
+
+
+def test_deterministic(dev):
+    lens = synth.random_lengths(50000, seed=11, mean=12, p_empty=0.3, p_long=0.001,
+                                long_len=30000)
+    A = synth.from_lengths(lens, 20000, seed=11)
+    x = synth.sym_vector(20000, seed=12)
+    api, C = _api()
+    Ad = api.to_device(A.row_ptr, A.col, A.val, A.n, dev)
+    xd = torch.as_tensor(x, device=dev)
+    y1 = api.spmv_f64(Ad, xd).cpu().numpy()
+    y2 = api.spmv_f64(Ad, xd).cpu().numpy()
+    assert np.array_equal(y1.view(np.int64), y2.view(np.int64))
+
+
+def test_host_buffer_entry_point(dev):
+    A, x = synth.workload("uniform4096")
+    api, C = _api()
+    y_host = np.full(A.m, np.nan)
+    nbytes = C.ssspmv_host_buffer_bytes(A.m, A.n, A.nnz)
+    buf = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    rc = C.ssspmv_csr_f64_host(A.m, A.n, A.nnz, A.row_ptr, A.col, A.val, x, y_host,
+                               dev_buffer=buf)
+    assert rc == 0
+    Ad = api.to_device(A.row_ptr, A.col, A.val, A.n, dev)
+    y_dev = api.spmv_f64(Ad, torch.as_tensor(x, device=dev)).cpu().numpy()
+    assert np.array_equal(y_host, y_dev)
+
+
+def test_validate_csr(dev):
+    api, C = _api()
+    scratch = torch.zeros(4, dtype=torch.int32, device=dev)
+    rp = torch.tensor([0, 2, 2, 5], dtype=torch.int32, device=dev)
+    col = torch.tensor([0, 3, 1, 1, 2], dtype=torch.int32, device=dev)
+    assert C.ssspmv_validate_csr(3, 4, 5, rp, col, scratch) == 0
+    assert C.ssspmv_validate_csr(3, 3, 5, rp, col, scratch) == C.SSSPMV_EINVAL   # col 3 >= n
+    bad_rp = torch.tensor([0, 3, 2, 5], dtype=torch.int32, device=dev)
+    assert C.ssspmv_validate_csr(3, 4, 5, bad_rp, col, scratch) == C.SSSPMV_EINVAL
+    assert C.ssspmv_validate_csr(3, 4, 4, rp, col, scratch) == C.SSSPMV_EINVAL   # rp[m] != nnz
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads in the launch configuration the bench times (auto W, S)
+
+@pytest.mark.parametrize("name", ["stencil160", "rmat22"])
+def test_full_size_workloads(dev, name):
+    A, x = synth.workload(name)
+    api, C = _api()
+    Ad = api.to_device(A.row_ptr, A.col, A.val, A.n, dev)
+    xd = torch.as_tensor(x, device=dev)
+    out = api.spmv_f64_debug(Ad, xd)
+    yref, s = oracle.spmv_dot2(A.row_ptr, A.col, A.val, x)
+    y = out["y"]
+    assert np.all(np.abs(y - yref) <= TOL * s)
+    assert np.all(y[s == 0] == 0.0)
+    L = out["shape"]["L"]
+    toff = oracle.tile_offsets(A.row_ptr, L)
+    assert np.array_equal(out["tile_offset"], toff)
+    dirty, nseg = oracle.tile_flags(A.row_ptr, L, toff)
+    assert np.array_equal((out["tile_info"] >> 31).astype(np.uint8), dirty)
+    assert np.array_equal((out["tile_info"] & 0x7FFFFFFF).astype(np.int32), nseg)
+    # the descriptor on a sample of tiles spread over the matrix
+    idx = np.unique(np.linspace(0, out["shape"]["ntiles"] - 1, 4001).astype(np.int64))
+    d = oracle.descriptors(A.row_ptr, L, toff)
+    assert np.array_equal(out["desc"][idx], d[idx])
+    # the timed entry point gives the same y as the debug one
+    y2 = api.spmv_f64(Ad, xd).cpu().numpy()
+    assert np.array_equal(y, y2)
