@@ -2,15 +2,9 @@
 
 The compute path is ``libssspmv.so`` (CUDA for sm_103a, C ABI declared in
 ``include/ssspmv.h``); ``ssspmv`` is its ctypes binding and ``api`` a small
-torch-facing convenience layer (device allocations and streams only).
+torch-facing convenience layer (device allocations and streams only,
+imported on demand: ``from paper_1504_06474_gb300 import api``).
 """
 from . import ssspmv  # noqa: F401
 
 __all__ = ["ssspmv", "api"]
-
-
-def __getattr__(name):
-    if name == "api":
-        from . import api
-        return api
-    raise AttributeError(name)

@@ -103,3 +103,10 @@ def test_empty_matrix_is_a_noop(lib):
 def test_opts_struct_layout(lib):
     assert ctypes.sizeof(S.ssspmv_opts) == 24
     assert S.ssspmv_opts.stage_events.offset == 16
+
+
+def test_torch_layer_imports(lib):
+    pytest.importorskip("torch")
+    from paper_1504_06474_gb300 import api, ssspmv
+    assert callable(api.spmv_f64) and callable(api.spmv_f64_debug)
+    assert api._c is ssspmv
