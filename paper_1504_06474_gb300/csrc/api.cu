@@ -17,6 +17,27 @@ int f64_run(Call &c);
 
 static thread_local int g_last_cuda_error = 0;
 
+typedef int (*cu_event_record_t)(void *, void *);
+
+cudaError_t record_event(cudaEvent_t ev, cudaStream_t s)
+{
+    static cu_event_record_t fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuEventRecord", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<cu_event_record_t>(p);
+        else
+            (void)cudaGetLastError();
+        looked = true;
+    }
+    if (fn) return fn((void *)ev, (void *)s) == 0 ? cudaSuccess : cudaErrorInvalidResourceHandle;
+    return cudaEventRecord(ev, s);
+}
+
 int record_cuda_error(cudaError_t e)
 {
     g_last_cuda_error = (int)e;

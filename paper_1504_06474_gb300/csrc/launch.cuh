@@ -24,6 +24,10 @@ struct Call {
 
 int record_cuda_error(cudaError_t e);  // api.cu: remembers e, returns SSSPMV_ECUDA
 int device_sm_count();                 // api.cu: SMs of the current device (cached)
+// api.cu: records a caller-owned event on the stream through the driver entry
+// point (caller events may come from another CUDA runtime instance in the
+// process, e.g. a framework's; driver handles are valid for every instance)
+cudaError_t record_event(cudaEvent_t ev, cudaStream_t s);
 
 constexpr int kZeroBlocks = 32;
 
@@ -85,13 +89,15 @@ int run_shape(const Call &c)
     void *sval = ws + l.off_sync_val;
     void *tval = ws + l.off_tail_val;
     int32_t *tflag = reinterpret_cast<int32_t *>(ws + l.off_tail_flag);
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
 
-    if (c.ev) cudaEventRecord(c.ev[0], c.stream);
+    if (c.ev && (e = record_event(c.ev[0], c.stream)) != cudaSuccess)
+        return record_cuda_error(e);
     {
         launch_partition(c.row_ptr, c.m, c.nnz, l.L, l.ntiles, toff, err, c.stream);
     }
-    if (c.ev) cudaEventRecord(c.ev[1], c.stream);
+    if (c.ev && (e = record_event(c.ev[1], c.stream)) != cudaSuccess)
+        return record_cuda_error(e);
     if (l.ntiles > 0) {
         SegsumArgs a;
         a.row_ptr = c.row_ptr;
@@ -130,7 +136,8 @@ int run_shape(const Call &c)
                             cudaMemcpyDeviceToDevice, c.stream);
         if (e != cudaSuccess) return record_cuda_error(e);
     }
-    if (c.ev) cudaEventRecord(c.ev[2], c.stream);
+    if (c.ev && (e = record_event(c.ev[2], c.stream)) != cudaSuccess)
+        return record_cuda_error(e);
     {
         CalibArgs a;
         a.row_ptr = c.row_ptr;
@@ -153,7 +160,8 @@ int run_shape(const Call &c)
         const unsigned grid = (unsigned)(a.nblk_tiles + a.nblk_sync + a.nblk_zero);
         calibrate_kernel<P><<<grid, kCalibWarps * 32, 0, c.stream>>>(a);
     }
-    if (c.ev) cudaEventRecord(c.ev[3], c.stream);
+    if (c.ev && (e = record_event(c.ev[3], c.stream)) != cudaSuccess)
+        return record_cuda_error(e);
     e = cudaGetLastError();
     if (e != cudaSuccess) return record_cuda_error(e);
     return SSSPMV_OK;

@@ -17,6 +17,7 @@
 // 8 bytes are still a multiple of 16 bytes for the bulk copies.
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "layout.h"
@@ -36,11 +37,71 @@ struct F64 {
     __device__ static __forceinline__ acc_t fma(val_t v, x_t x, acc_t a) { return __fma_rn(v, x, a); }
     __device__ static __forceinline__ acc_t add(acc_t a, acc_t b) { return __dadd_rn(a, b); }
     __device__ static __forceinline__ y_t out(acc_t a) { return a; }
+    __device__ static __forceinline__ double to_f64(acc_t a) { return a; }
+    __device__ static __forceinline__ acc_t shfl_up(acc_t a, int d)
+    {
+        return __shfl_up_sync(FULL, a, d);
+    }
     __device__ static __forceinline__ x_t gather(const x_t *x, int32_t c, uint64_t pol)
     {
         return ldg_keep(x + c, pol);
     }
 };
+
+// FP32 accumulation carried as an unevaluated sum s + c: each product is
+// split exactly by TwoProduct (fused multiply-add) and added with TwoSum
+// (Knuth), the Dot2 scheme of Ogita, Rump and Oishi (SIAM J. Sci. Comput.
+// 2005) in single precision.
+struct CompF32 {
+    float s, c;
+};
+
+__device__ __forceinline__ CompF32 comp_add(CompF32 a, CompF32 b)
+{
+    const float s = __fadd_rn(a.s, b.s);
+    const float z = __fadd_rn(s, -a.s);
+    const float t = __fadd_rn(__fadd_rn(a.s, -__fadd_rn(s, -z)), __fadd_rn(b.s, -z));
+    return CompF32{s, __fadd_rn(__fadd_rn(a.c, b.c), t)};
+}
+
+__device__ __forceinline__ CompF32 comp_fma(float v, float x, CompF32 a)
+{
+    const float p = __fmul_rn(v, x);
+    const float e = __fmaf_rn(v, x, -p);        // v*x - p exactly
+    const float s = __fadd_rn(a.s, p);
+    const float z = __fadd_rn(s, -a.s);
+    const float t = __fadd_rn(__fadd_rn(a.s, -__fadd_rn(s, -z)), __fadd_rn(p, -z));
+    return CompF32{s, __fadd_rn(a.c, __fadd_rn(t, e))};
+}
+
+template <class V>
+struct CompF32Traits {
+    using val_t = V;
+    using x_t = float;
+    using y_t = float;
+    using acc_t = CompF32;
+    __device__ static __forceinline__ float widen(float v) { return v; }
+    __device__ static __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ static __forceinline__ acc_t zero() { return CompF32{0.f, 0.f}; }
+    __device__ static __forceinline__ acc_t fma(val_t v, x_t x, acc_t a)
+    {
+        return comp_fma(widen(v), x, a);
+    }
+    __device__ static __forceinline__ acc_t add(acc_t a, acc_t b) { return comp_add(a, b); }
+    __device__ static __forceinline__ y_t out(acc_t a) { return __fadd_rn(a.s, a.c); }
+    __device__ static __forceinline__ double to_f64(acc_t a) { return (double)a.s + (double)a.c; }
+    __device__ static __forceinline__ acc_t shfl_up(acc_t a, int d)
+    {
+        return CompF32{__shfl_up_sync(FULL, a.s, d), __shfl_up_sync(FULL, a.c, d)};
+    }
+    __device__ static __forceinline__ x_t gather(const x_t *x, int32_t c, uint64_t pol)
+    {
+        return ldg_keep(x + c, pol);
+    }
+};
+
+using F32C = CompF32Traits<float>;           // FP32 val, x, y
+using BF16C = CompF32Traits<__nv_bfloat16>;  // BF16 val, FP32 x, y
 
 // ---------------------------------------------------------------------------
 // kernel (a): partition (Sec. 3.2: binary search of the tile boundaries on
@@ -289,17 +350,17 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
         A C = v;
         if (span <= 4) {
             for (int d = 1; d <= span; ++d) {
-                const A o = __shfl_up_sync(FULL, v, d);
+                const A o = P::shfl_up(v, d);
                 if (lane - d >= first) C = P::add(C, o);
             }
         } else {
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
-                const A o = __shfl_up_sync(FULL, C, d);
+                const A o = P::shfl_up(C, d);
                 if (lane - d >= first) C = P::add(C, o);
             }
         }
-        const A Cprev = __shfl_up_sync(FULL, C, 1);
+        const A Cprev = P::shfl_up(C, 1);
         // a lane with a head closes the segment left open before it
         if (has && lane > 0) emit(idx0 - 1, P::add(Cprev, pre));
         // the tile's last segment: stored, or carried if row `stop` goes on
@@ -328,12 +389,11 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
     }
     __syncwarp();
     F = *slot_f;
-    G = __shfl_sync(FULL, G, 31);
-    hasG = __shfl_sync(FULL, hasG, 31);
-    if (lane == 0) {
+    if (lane == 31) {
+        // synchronizer record of this bunch; its sums are finished in FP64
         a.sync_idx[w] = rF;
-        static_cast<A *>(a.sync_val)[w] = F;
-        static_cast<A *>(a.tail_val)[w] = hasG ? G : P::zero();
+        static_cast<double *>(a.sync_val)[w] = P::to_f64(F);
+        static_cast<double *>(a.tail_val)[w] = hasG ? P::to_f64(G) : 0.0;
         a.tail_flag[w] = hasG ? 1 : 0;
     }
 }
@@ -422,19 +482,19 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
         if (w >= a.nbunches) return;
         const int32_t r = __ldg(a.sync_idx + w);
         if (w > 0 && __ldg(a.sync_idx + w - 1) == r) return;
-        const A *sv = static_cast<const A *>(a.sync_val);
+        const double *sv = static_cast<const double *>(a.sync_val);
         double acc = 0.0;  // calibration sums are kept in FP64
         for (int64_t base = w;; base += 32) {
             const int64_t ww = base + lane;
             const bool in = ww < a.nbunches && __ldg(a.sync_idx + ww) == r;
-            if (in) acc += (double)sv[ww];
+            if (in) acc += sv[ww];
             if (__popc(__ballot_sync(FULL, in)) < 32) break;
         }
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1) acc += __shfl_xor_sync(FULL, acc, d);
         if (lane == 0) {
             if (w > 0 && __ldg(a.tail_flag + w - 1))
-                acc += (double)static_cast<const A *>(a.tail_val)[w - 1];
+                acc += static_cast<const double *>(a.tail_val)[w - 1];
             if (r >= 0 && r < a.m) y[r] = (Y)acc;
             else atomicOr(a.err, SSSPMV_DEV_RANGE);
         }
