@@ -18,7 +18,6 @@ paper's CPU row-block method) on this machine's host cores instead.
 from __future__ import annotations
 
 import argparse
-import ctypes
 import json
 import os
 import statistics
@@ -234,18 +233,13 @@ def run_ours(args):
         step(plain)
     torch.cuda.synchronize(dev)
 
-    # per-step events recorded by the library on the launching stream
+    # per-step stage boundaries recorded by the library's own events on the
+    # launching stream
     K = args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
-    arrs = [(ctypes.c_void_p * 4)(*[e.cuda_event for e in row]) for row in evs]
-    opts_k = [C.make_opts(W=args.tile_w, S=args.tile_s, stage_events=ctypes.addressof(a))
-              for a in arrs]
-    for row in evs:  # materialise the CUDA events
-        for e in row:
-            e.record(stream)
-    torch.cuda.synchronize(dev)
+    timer = C.ssspmv_timer_create(K)
+    opts_t = C.make_opts(W=args.tile_w, S=args.tile_s, timer=timer)
 
-    sampler = ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    sampler = ClockSampler(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -254,17 +248,20 @@ def run_ours(args):
     t_wall = time.perf_counter()
     for k in range(K):
         flush.zero_()
-        step(opts_k[k])
+        step(opts_t)
     torch.cuda.synchronize(dev)
     t_wall = time.perf_counter() - t_wall
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
+    times = C.ssspmv_timer_read(timer, K)
+    C.ssspmv_timer_destroy(timer)
+    assert len(times) == K
 
-    per_step = [evs[k][0].elapsed_time(evs[k][3]) for k in range(K)]       # ms
-    seg = [evs[k][1].elapsed_time(evs[k][2]) for k in range(K)]
-    part = [evs[k][0].elapsed_time(evs[k][1]) for k in range(K)]
-    cal = [evs[k][2].elapsed_time(evs[k][3]) for k in range(K)]
+    part = [t[0] for t in times]                                             # ms
+    seg = [t[1] for t in times]
+    cal = [t[2] for t in times]
+    per_step = [t[3] for t in times]
     t_total = sum(per_step) / 1e3                                            # s
     if world > 1:
         tt = torch.tensor([t_total], dtype=torch.float64, device=dev)

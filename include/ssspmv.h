@@ -71,13 +71,28 @@ typedef struct ssspmv_opts {
     int32_t S;         /* tiles per thread-bunch (warp); 0 = one wave of warps */
     int32_t validate;  /* reserved, must be 0 (use ssspmv_validate_csr) */
     int32_t reserved;
-    void   *stage_events; /* optional cudaEvent_t[4] (as void*): recorded on the
-                             stream before kernel (a), before (b), before (c)
-                             and after (c); NULL = none */
+    void   *timer;     /* optional ssspmv_timer*: the call records its kernel
+                          boundaries into the timer's next slot; NULL = none */
 } ssspmv_opts;
 
+/* Stage timing with events owned by this library (events created by another
+ * CUDA runtime instance in the process cannot be recorded from here).  A
+ * timer holds `capacity` slots; every call given the timer in opts->timer
+ * records 4 events on its stream into the next free slot (before kernel (a),
+ * before (b), before (c), after (c)); calls beyond capacity are not timed.
+ * Not thread safe: one timer per stream. */
+typedef struct ssspmv_timer ssspmv_timer;
+int ssspmv_timer_create(int32_t capacity, ssspmv_timer **out);
+void ssspmv_timer_destroy(ssspmv_timer *t);
+/* forget recorded slots (the events are reused) */
+void ssspmv_timer_reset(ssspmv_timer *t);
+/* waits for the recorded events and writes, for slot i < *count (at most cap
+ * slots): ms[4i] = kernel (a), ms[4i+1] = kernel (b), ms[4i+2] = kernel (c),
+ * ms[4i+3] = the whole call, in milliseconds */
+int ssspmv_timer_read(ssspmv_timer *t, float *ms, int32_t cap, int32_t *count);
+
 /* The tile shape and bunch count a call with these arguments would use.
- * val_bytes = sizeof the stored value type (8 for FP64).  Any output pointer
+ * val_bytes = sizeof the stored value type: 8 (FP64), 4 (FP32) or 2 (BF16).  Any output pointer
  * may be NULL.  Returns SSSPMV_OK or SSSPMV_EINVAL/EUNSUPPORTED. */
 int ssspmv_plan_shape(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_opts *opts,
                       int32_t *W, int32_t *L, int32_t *S, int64_t *ntiles, int64_t *nbunches);
@@ -94,6 +109,22 @@ int ssspmv_csr_f64(int32_t m, int32_t n, int32_t nnz,
                    const int32_t *row_ptr, const int32_t *col_idx, const double *val,
                    const double *x, double *y,
                    const ssspmv_opts *opts, void *workspace, size_t ws_bytes, void *stream);
+
+/* y = A x with FP32 val, x and y.  Products are split exactly (TwoProduct)
+ * and summed with TwoSum into an unevaluated FP32 pair per segment; the
+ * synchronizer sums of rows crossing bunches are finished in FP64.
+ * workspace: ssspmv_workspace_bytes(m, nnz, 4, opts) bytes. */
+int ssspmv_csr_f32(int32_t m, int32_t n, int32_t nnz,
+                   const int32_t *row_ptr, const int32_t *col_idx, const float *val,
+                   const float *x, float *y,
+                   const ssspmv_opts *opts, void *workspace, size_t ws_bytes, void *stream);
+
+/* y = A x with BF16 val (raw bfloat16 bits), FP32 x and y, accumulated as in
+ * ssspmv_csr_f32.  workspace: ssspmv_workspace_bytes(m, nnz, 2, opts) bytes. */
+int ssspmv_csr_bf16f32(int32_t m, int32_t n, int32_t nnz,
+                       const int32_t *row_ptr, const int32_t *col_idx, const uint16_t *val,
+                       const float *x, float *y,
+                       const ssspmv_opts *opts, void *workspace, size_t ws_bytes, void *stream);
 
 /* The same product with HOST arrays (pageable or pinned): copies row_ptr,
  * col_idx, val and x into `dev_buffer` (device memory of at least

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <new>
 
 #include "launch.cuh"
 
@@ -14,29 +15,34 @@ namespace ssspmv {
 int f64_supported_w(int32_t *out, int cap);
 int f64_resolve(Layout &l, int32_t S_opt);
 int f64_run(Call &c);
+int f32_supported_w(int32_t *out, int cap);
+int f32_resolve(Layout &l, int32_t S_opt);
+int f32_run(Call &c);
+int bf16_supported_w(int32_t *out, int cap);
+int bf16_resolve(Layout &l, int32_t S_opt);
+int bf16_run(Call &c);
+
+// one entry per stored value type; the value size identifies the precision
+struct Prec {
+    int32_t val_bytes;
+    int (*supported)(int32_t *, int);
+    int (*resolve)(Layout &, int32_t);
+    int (*run)(Call &);
+};
+static const Prec kPrecs[] = {
+    {8, f64_supported_w, f64_resolve, f64_run},
+    {4, f32_supported_w, f32_resolve, f32_run},
+    {2, bf16_supported_w, bf16_resolve, bf16_run},
+};
+
+static const Prec *prec_for(int32_t val_bytes)
+{
+    for (const Prec &p : kPrecs)
+        if (p.val_bytes == val_bytes) return &p;
+    return nullptr;
+}
 
 static thread_local int g_last_cuda_error = 0;
-
-typedef int (*cu_event_record_t)(void *, void *);
-
-cudaError_t record_event(cudaEvent_t ev, cudaStream_t s)
-{
-    static cu_event_record_t fn = nullptr;
-    static bool looked = false;
-    if (!looked) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuEventRecord", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<cu_event_record_t>(p);
-        else
-            (void)cudaGetLastError();
-        looked = true;
-    }
-    if (fn) return fn((void *)ev, (void *)s) == 0 ? cudaSuccess : cudaErrorInvalidResourceHandle;
-    return cudaEventRecord(ev, s);
-}
 
 int record_cuda_error(cudaError_t e)
 {
@@ -68,8 +74,9 @@ int device_sm_count()
 static int resolve_w(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_opts *o, int32_t *W)
 {
     int32_t ws[16];
-    int n = 0;
-    if (val_bytes == 8) n = f64_supported_w(ws, 16);
+    const Prec *pr = prec_for(val_bytes);
+    if (!pr) return SSSPMV_EUNSUPPORTED;
+    int n = pr->supported(ws, 16);
     if (n <= 0) return SSSPMV_EUNSUPPORTED;
     if (n > 16) n = 16;
     if (o && o->W != 0) {
@@ -111,6 +118,23 @@ static int make_layout(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_o
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+}  // namespace ssspmv
+
+struct ssspmv_timer {
+    int32_t capacity = 0;
+    int32_t used = 0;
+    cudaEvent_t *ev = nullptr;  // 4 per slot
+};
+
+namespace ssspmv {
+
+// the 4 events of the timer's next slot, or null when it is full
+static cudaEvent_t *timer_next_slot(ssspmv_timer *t)
+{
+    if (!t || t->used >= t->capacity) return nullptr;
+    return t->ev + 4 * (t->used++);
+}
+
 static int check_csr_args(int32_t m, int32_t n, int32_t nnz, const void *row_ptr,
                           const void *col, const void *val, const void *x, const void *y)
 {
@@ -122,20 +146,22 @@ static int check_csr_args(int32_t m, int32_t n, int32_t nnz, const void *row_ptr
     return SSSPMV_OK;
 }
 
-static int run_f64_call(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr,
-                        const int32_t *col, const double *val, const double *x, double *y,
-                        const ssspmv_opts *opts, void *ws, size_t ws_bytes, void *stream,
-                        uint32_t *dbg_desc, double *dbg_yspec, Layout *out_layout)
+static int run_call(int32_t val_bytes, int32_t m, int32_t n, int32_t nnz,
+                    const int32_t *row_ptr, const int32_t *col, const void *val, const void *x,
+                    void *y, const ssspmv_opts *opts, void *ws, size_t ws_bytes, void *stream,
+                    uint32_t *dbg_desc, void *dbg_yspec, Layout *out_layout)
 {
+    const Prec *pr = prec_for(val_bytes);
+    if (!pr) return SSSPMV_EUNSUPPORTED;
     int rc = check_csr_args(m, n, nnz, row_ptr, col, val, x, y);
     if (rc) return rc;
     Layout l;
-    rc = make_layout(m, nnz, 8, opts, l);
+    rc = make_layout(m, nnz, val_bytes, opts, l);
     if (rc) return rc;
     if (out_layout) *out_layout = l;
     if (m == 0) return SSSPMV_OK;
     if (!ws || ws_bytes < l.total || ((uintptr_t)ws & 255u)) return SSSPMV_EWORKSPACE;
-    rc = f64_resolve(l, opts ? opts->S : 0);
+    rc = pr->resolve(l, opts ? opts->S : 0);
     if (rc) return rc;
     if (l.nbunches > l.nbunch_cap) return SSSPMV_EWORKSPACE;
     if (out_layout) *out_layout = l;
@@ -151,10 +177,11 @@ static int run_f64_call(int32_t m, int32_t n, int32_t nnz, const int32_t *row_pt
     c.lay = l;
     c.ws = static_cast<unsigned char *>(ws);
     c.stream = static_cast<cudaStream_t>(stream);
-    c.ev = (opts && opts->stage_events) ? static_cast<cudaEvent_t *>(opts->stage_events) : nullptr;
+    c.ev = (opts && opts->timer) ? timer_next_slot(static_cast<ssspmv_timer *>(opts->timer))
+                                 : nullptr;
     c.dbg_desc = dbg_desc;
     c.dbg_yspec = dbg_yspec;
-    return f64_run(c);
+    return pr->run(c);
 }
 
 // ---------------------------------------------------------------------------
@@ -181,6 +208,65 @@ using namespace ssspmv;
 extern "C" {
 
 int ssspmv_version(void) { return 10000; }
+
+int ssspmv_timer_create(int32_t capacity, ssspmv_timer **out)
+{
+    if (!out || capacity <= 0) return SSSPMV_EINVAL;
+    *out = nullptr;
+    ssspmv_timer *t = new (std::nothrow) ssspmv_timer;
+    if (!t) return SSSPMV_EINVAL;
+    t->ev = new (std::nothrow) cudaEvent_t[4 * (size_t)capacity];
+    if (!t->ev) { delete t; return SSSPMV_EINVAL; }
+    for (int32_t i = 0; i < 4 * capacity; ++i) {
+        cudaError_t e = cudaEventCreate(&t->ev[i]);
+        if (e != cudaSuccess) {
+            for (int32_t j = 0; j < i; ++j) cudaEventDestroy(t->ev[j]);
+            delete[] t->ev;
+            delete t;
+            return record_cuda_error(e);
+        }
+    }
+    t->capacity = capacity;
+    *out = t;
+    return SSSPMV_OK;
+}
+
+void ssspmv_timer_destroy(ssspmv_timer *t)
+{
+    if (!t) return;
+    for (int32_t i = 0; i < 4 * t->capacity; ++i) cudaEventDestroy(t->ev[i]);
+    delete[] t->ev;
+    delete t;
+}
+
+void ssspmv_timer_reset(ssspmv_timer *t)
+{
+    if (t) t->used = 0;
+}
+
+int ssspmv_timer_read(ssspmv_timer *t, float *ms, int32_t cap, int32_t *count)
+{
+    if (!t) return SSSPMV_EINVAL;
+    const int32_t n = t->used < cap ? t->used : cap;
+    if (count) *count = t->used;
+    for (int32_t i = 0; i < n; ++i) {
+        cudaEvent_t *e = t->ev + 4 * i;
+        cudaError_t r = cudaEventSynchronize(e[3]);
+        float a = 0, b = 0, c = 0, w = 0;
+        if (r == cudaSuccess) r = cudaEventElapsedTime(&a, e[0], e[1]);
+        if (r == cudaSuccess) r = cudaEventElapsedTime(&b, e[1], e[2]);
+        if (r == cudaSuccess) r = cudaEventElapsedTime(&c, e[2], e[3]);
+        if (r == cudaSuccess) r = cudaEventElapsedTime(&w, e[0], e[3]);
+        if (r != cudaSuccess) return record_cuda_error(r);
+        if (ms) {
+            ms[4 * i + 0] = a;
+            ms[4 * i + 1] = b;
+            ms[4 * i + 2] = c;
+            ms[4 * i + 3] = w;
+        }
+    }
+    return SSSPMV_OK;
+}
 
 int ssspmv_last_cuda_error(void) { return g_last_cuda_error; }
 
@@ -210,11 +296,12 @@ int ssspmv_supported_w(int32_t *out, int32_t cap, int32_t *count)
 int ssspmv_plan_shape(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_opts *opts,
                       int32_t *W, int32_t *L, int32_t *S, int64_t *ntiles, int64_t *nbunches)
 {
-    if (val_bytes != 8) return SSSPMV_EUNSUPPORTED;
+    const Prec *pr = prec_for(val_bytes);
+    if (!pr) return SSSPMV_EUNSUPPORTED;
     Layout l;
     int rc = make_layout(m, nnz, val_bytes, opts, l);
     if (rc) return rc;
-    rc = f64_resolve(l, opts ? opts->S : 0);
+    rc = pr->resolve(l, opts ? opts->S : 0);
     if (rc) return rc;
     if (W) *W = l.W;
     if (L) *L = l.L;
@@ -226,7 +313,7 @@ int ssspmv_plan_shape(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_op
 
 size_t ssspmv_workspace_bytes(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_opts *opts)
 {
-    if (val_bytes != 8) return 0;
+    if (!prec_for(val_bytes)) return 0;
     Layout l;
     if (make_layout(m, nnz, val_bytes, opts, l)) return 0;
     return l.total;
@@ -236,8 +323,24 @@ int ssspmv_csr_f64(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr,
                    const int32_t *col_idx, const double *val, const double *x, double *y,
                    const ssspmv_opts *opts, void *workspace, size_t ws_bytes, void *stream)
 {
-    return run_f64_call(m, n, nnz, row_ptr, col_idx, val, x, y, opts, workspace, ws_bytes,
-                        stream, nullptr, nullptr, nullptr);
+    return run_call(8, m, n, nnz, row_ptr, col_idx, val, x, y, opts, workspace, ws_bytes, stream,
+                    nullptr, nullptr, nullptr);
+}
+
+int ssspmv_csr_f32(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr,
+                   const int32_t *col_idx, const float *val, const float *x, float *y,
+                   const ssspmv_opts *opts, void *workspace, size_t ws_bytes, void *stream)
+{
+    return run_call(4, m, n, nnz, row_ptr, col_idx, val, x, y, opts, workspace, ws_bytes, stream,
+                    nullptr, nullptr, nullptr);
+}
+
+int ssspmv_csr_bf16f32(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr,
+                       const int32_t *col_idx, const uint16_t *val, const float *x, float *y,
+                       const ssspmv_opts *opts, void *workspace, size_t ws_bytes, void *stream)
+{
+    return run_call(2, m, n, nnz, row_ptr, col_idx, val, x, y, opts, workspace, ws_bytes, stream,
+                    nullptr, nullptr, nullptr);
 }
 
 int ssspmv_csr_f64_debug(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr,
@@ -247,8 +350,8 @@ int ssspmv_csr_f64_debug(int32_t m, int32_t n, int32_t nnz, const int32_t *row_p
                          int32_t *sync_idx, double *y_spec)
 {
     Layout l;
-    int rc = run_f64_call(m, n, nnz, row_ptr, col_idx, val, x, y, opts, workspace, ws_bytes,
-                          stream, desc, y_spec, &l);
+    int rc = run_call(8, m, n, nnz, row_ptr, col_idx, val, x, y, opts, workspace, ws_bytes, stream,
+                      desc, y_spec, &l);
     if (rc) return rc;
     if (m == 0) return SSSPMV_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

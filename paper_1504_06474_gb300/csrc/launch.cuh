@@ -17,17 +17,13 @@ struct Call {
     Layout lay;
     unsigned char *ws = nullptr;
     cudaStream_t stream = nullptr;
-    cudaEvent_t *ev = nullptr;       // 4 events or null
+    cudaEvent_t *ev = nullptr;       // 4 library-owned events or null
     uint32_t *dbg_desc = nullptr;    // ntiles*W words or null
     void *dbg_yspec = nullptr;       // m values or null
 };
 
 int record_cuda_error(cudaError_t e);  // api.cu: remembers e, returns SSSPMV_ECUDA
 int device_sm_count();                 // api.cu: SMs of the current device (cached)
-// api.cu: records a caller-owned event on the stream through the driver entry
-// point (caller events may come from another CUDA runtime instance in the
-// process, e.g. a framework's; driver handles are valid for every instance)
-cudaError_t record_event(cudaEvent_t ev, cudaStream_t s);
 
 constexpr int kZeroBlocks = 32;
 
@@ -91,12 +87,12 @@ int run_shape(const Call &c)
     int32_t *tflag = reinterpret_cast<int32_t *>(ws + l.off_tail_flag);
     cudaError_t e = cudaSuccess;
 
-    if (c.ev && (e = record_event(c.ev[0], c.stream)) != cudaSuccess)
+    if (c.ev && (e = cudaEventRecord(c.ev[0], c.stream)) != cudaSuccess)
         return record_cuda_error(e);
     {
         launch_partition(c.row_ptr, c.m, c.nnz, l.L, l.ntiles, toff, err, c.stream);
     }
-    if (c.ev && (e = record_event(c.ev[1], c.stream)) != cudaSuccess)
+    if (c.ev && (e = cudaEventRecord(c.ev[1], c.stream)) != cudaSuccess)
         return record_cuda_error(e);
     if (l.ntiles > 0) {
         SegsumArgs a;
@@ -136,7 +132,7 @@ int run_shape(const Call &c)
                             cudaMemcpyDeviceToDevice, c.stream);
         if (e != cudaSuccess) return record_cuda_error(e);
     }
-    if (c.ev && (e = record_event(c.ev[2], c.stream)) != cudaSuccess)
+    if (c.ev && (e = cudaEventRecord(c.ev[2], c.stream)) != cudaSuccess)
         return record_cuda_error(e);
     {
         CalibArgs a;
@@ -160,7 +156,7 @@ int run_shape(const Call &c)
         const unsigned grid = (unsigned)(a.nblk_tiles + a.nblk_sync + a.nblk_zero);
         calibrate_kernel<P><<<grid, kCalibWarps * 32, 0, c.stream>>>(a);
     }
-    if (c.ev && (e = record_event(c.ev[3], c.stream)) != cudaSuccess)
+    if (c.ev && (e = cudaEventRecord(c.ev[3], c.stream)) != cudaSuccess)
         return record_cuda_error(e);
     e = cudaGetLastError();
     if (e != cudaSuccess) return record_cuda_error(e);

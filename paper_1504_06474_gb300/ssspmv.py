@@ -37,7 +37,7 @@ class SsspmvError(RuntimeError):
 
 class ssspmv_opts(ctypes.Structure):
     _fields_ = [("W", ctypes.c_int32), ("S", ctypes.c_int32), ("validate", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("stage_events", ctypes.c_void_p)]
+                ("reserved", ctypes.c_int32), ("timer", ctypes.c_void_p)]
 
 
 _L = None
@@ -49,6 +49,8 @@ _SIGS = {
     "ssspmv_plan_shape": (ctypes.c_int, [i32, i32, i32, OPTS, P, P, P, P, P]),
     "ssspmv_workspace_bytes": (sz, [i32, i32, i32, OPTS]),
     "ssspmv_csr_f64": (ctypes.c_int, [i32, i32, i32, P, P, P, P, P, OPTS, P, sz, P]),
+    "ssspmv_csr_f32": (ctypes.c_int, [i32, i32, i32, P, P, P, P, P, OPTS, P, sz, P]),
+    "ssspmv_csr_bf16f32": (ctypes.c_int, [i32, i32, i32, P, P, P, P, P, OPTS, P, sz, P]),
     "ssspmv_host_buffer_bytes": (sz, [i32, i32, i32, OPTS]),
     "ssspmv_csr_f64_host": (ctypes.c_int, [i32, i32, i32, P, P, P, P, P, OPTS, P, sz, P]),
     "ssspmv_csr_f64_debug": (ctypes.c_int, [i32, i32, i32, P, P, P, P, P, OPTS, P, sz, P,
@@ -56,6 +58,10 @@ _SIGS = {
     "ssspmv_validate_csr": (ctypes.c_int, [i32, i32, i32, P, P, P, P]),
     "ssspmv_device_status": (ctypes.c_int, [P, sz, P, ctypes.c_int, P]),
     "ssspmv_supported_w": (ctypes.c_int, [P, i32, P]),
+    "ssspmv_timer_create": (ctypes.c_int, [i32, P]),
+    "ssspmv_timer_destroy": (None, [P]),
+    "ssspmv_timer_reset": (None, [P]),
+    "ssspmv_timer_read": (ctypes.c_int, [P, P, i32, P]),
     "ssspmv_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "ssspmv_last_cuda_error": (ctypes.c_int, []),
     "ssspmv_version": (ctypes.c_int, []),
@@ -112,10 +118,10 @@ def _stream(s):
     return s.cuda_stream
 
 
-def make_opts(W: int = 0, S: int = 0, stage_events=None) -> ssspmv_opts:
+def make_opts(W: int = 0, S: int = 0, timer=None) -> ssspmv_opts:
     o = ssspmv_opts()
     o.W, o.S, o.validate, o.reserved = W, S, 0, 0
-    o.stage_events = stage_events
+    o.timer = timer
     return o
 
 
@@ -151,6 +157,24 @@ def ssspmv_csr_f64(m, n, nnz, row_ptr, col_idx, val, x, y, opts=None, workspace=
     return _lib().ssspmv_csr_f64(m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(val), _ptr(x),
                                  _ptr(y), _opts(opts), _ptr(workspace), ws_bytes,
                                  _stream(stream))
+
+
+def ssspmv_csr_f32(m, n, nnz, row_ptr, col_idx, val, x, y, opts=None, workspace=None,
+                   ws_bytes=None, stream=None) -> int:
+    if ws_bytes is None:
+        ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    return _lib().ssspmv_csr_f32(m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(val), _ptr(x),
+                                 _ptr(y), _opts(opts), _ptr(workspace), ws_bytes,
+                                 _stream(stream))
+
+
+def ssspmv_csr_bf16f32(m, n, nnz, row_ptr, col_idx, val, x, y, opts=None, workspace=None,
+                       ws_bytes=None, stream=None) -> int:
+    if ws_bytes is None:
+        ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    return _lib().ssspmv_csr_bf16f32(m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(val),
+                                     _ptr(x), _ptr(y), _opts(opts), _ptr(workspace), ws_bytes,
+                                     _stream(stream))
 
 
 def ssspmv_host_buffer_bytes(m, n, nnz, opts=None) -> int:
@@ -197,6 +221,29 @@ def ssspmv_supported_w() -> list[int]:
     cnt = i32()
     _lib().ssspmv_supported_w(buf, 16, ctypes.byref(cnt))
     return [buf[i] for i in range(min(cnt.value, 16))]
+
+
+def ssspmv_timer_create(capacity: int) -> int:
+    h = ctypes.c_void_p()
+    check(_lib().ssspmv_timer_create(capacity, ctypes.byref(h)), "ssspmv_timer_create")
+    return h.value
+
+
+def ssspmv_timer_destroy(timer: int) -> None:
+    _lib().ssspmv_timer_destroy(timer)
+
+
+def ssspmv_timer_reset(timer: int) -> None:
+    _lib().ssspmv_timer_reset(timer)
+
+
+def ssspmv_timer_read(timer: int, cap: int):
+    """List of (partition, segsum, calibrate, whole call) times in ms."""
+    buf = (ctypes.c_float * (4 * max(cap, 1)))()
+    cnt = i32()
+    check(_lib().ssspmv_timer_read(timer, buf, cap, ctypes.byref(cnt)), "ssspmv_timer_read")
+    n = min(cnt.value, cap)
+    return [tuple(buf[4 * i + j] for j in range(4)) for i in range(n)]
 
 
 def ssspmv_strerror(code: int) -> str:

@@ -102,7 +102,7 @@ def test_empty_matrix_is_a_noop(lib):
 
 def test_opts_struct_layout(lib):
     assert ctypes.sizeof(S.ssspmv_opts) == 24
-    assert S.ssspmv_opts.stage_events.offset == 16
+    assert S.ssspmv_opts.timer.offset == 16
 
 
 def test_torch_layer_imports(lib):

@@ -222,3 +222,25 @@ def test_full_size_workloads(dev, name):
     # the timed entry point gives the same y as the debug one
     y2 = api.spmv_f64(Ad, xd).cpu().numpy()
     assert np.array_equal(y, y2)
+
+
+def test_stage_timer(dev):
+    A, x = synth.workload("uniform4096")
+    api, C = _api()
+    Ad = api.to_device(A.row_ptr, A.col, A.val, A.n, dev)
+    xd = torch.as_tensor(x, device=dev)
+    timer = C.ssspmv_timer_create(3)
+    try:
+        opts = C.make_opts(timer=timer)
+        ws = api.workspace_for(Ad, opts, device=dev)
+        for _ in range(4):          # the fourth call exceeds the capacity: untimed
+            api.spmv_f64(Ad, xd, opts=opts, workspace=ws)
+        times = C.ssspmv_timer_read(timer, 8)
+        assert len(times) == 3
+        for a, b, c, whole in times:
+            assert min(a, b, c) >= 0 and whole > 0
+            assert abs((a + b + c) - whole) <= 1e-3 + 1e-3 * whole
+        C.ssspmv_timer_reset(timer)
+        assert C.ssspmv_timer_read(timer, 8) == []
+    finally:
+        C.ssspmv_timer_destroy(timer)
