@@ -15,6 +15,7 @@ by synthetic matrices because the real collection is not available):
 * ``stencil160``   27-point stencil on a 160^3 grid (4,096,000 rows,
   109,215,352 nnz), diagonal 26.0, off-diagonals -1.0 + U[-0.01, 0.01),
   x ~ U[-1, 1), seed 1.
+* ``stencil<k>``   the same stencil on a k^3 grid (smaller cases for profiling).
 * ``rmat22``       R-MAT scale 22, edge factor 16, (0.57, 0.19, 0.19, 0.05),
   duplicates merged, self loops kept, one seeded row replaced by 1,000,000
   distinct uniform sorted columns, val and x ~ U[-1, 1), seed 2.
@@ -148,6 +149,11 @@ def workload(name: str) -> tuple[CSR, np.ndarray]:
     if name == "stencil160":
         A = stencil27(160, 160, 160, seed=1)
         A.name = "stencil160"
+        return A, sym_vector(A.n, seed=1)
+    if name.startswith("stencil") and name[7:].isdigit():
+        k = int(name[7:])          # 27-point stencil on k^3 (profiling sizes)
+        A = stencil27(k, k, k, seed=1)
+        A.name = name
         return A, sym_vector(A.n, seed=1)
     if name == "rmat22":
         A = rmat(22, 16, (0.57, 0.19, 0.19), seed=2, inject_len=1_000_000)
