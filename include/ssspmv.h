@@ -56,6 +56,7 @@ extern "C" {
 #define SSSPMV_ECUDA        -3  /* a CUDA call failed; see ssspmv_last_cuda_error() */
 #define SSSPMV_EDEVICE      -4  /* a kernel reported an inconsistency or a timed-out wait */
 #define SSSPMV_EUNSUPPORTED -5  /* tile shape not compiled in this build */
+#define SSSPMV_ETOOLARGE    -6  /* problem needs more scratch than ssspmv_csr_f64_noalloc has */
 
 /* Device error bits written by the kernels into the workspace (read with
  * ssspmv_device_status). */
@@ -125,6 +126,30 @@ int ssspmv_csr_bf16f32(int32_t m, int32_t n, int32_t nnz,
                        const int32_t *row_ptr, const int32_t *col_idx, const uint16_t *val,
                        const float *x, float *y,
                        const ssspmv_opts *opts, void *workspace, size_t ws_bytes, void *stream);
+
+/* Allocation-free FP64 product.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- code handed
+ * only device pointers for A, x and y with no allocator of its own (a plug-in
+ * inside another application's solver loop whose memory belongs to that
+ * application), or code that must not call cudaMalloc/cudaFree on its hot
+ * path because those calls can synchronise the device and stall other
+ * streams.  Same arguments and result as ssspmv_csr_f64, without the
+ * workspace: the workspace lives in a fixed device array of
+ * SSSPMV_NOALLOC_SCRATCH_BYTES owned by the library, held by every GPU that
+ * loads the library until the process exits.  Problems whose
+ * ssspmv_workspace_bytes(m, nnz, 8, opts) exceeds it are rejected with
+ * SSSPMV_ETOOLARGE before anything runs (8 MiB covers about 950,000 tiles
+ * with the automatic bunch count, e.g. nnz up to ~450M at W = 15).
+ * All calls on a device share the array and it keeps the last call's
+ * contents (the kernels rewrite every entry they read, so nothing needs
+ * clearing); calls that overlap on the GPU race on it -- order them on one
+ * stream.  The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress) with that device current; make it before any stream
+ * capture begins.  No call allocates device memory. */
+#define SSSPMV_NOALLOC_SCRATCH_BYTES (8u << 20)
+int ssspmv_csr_f64_noalloc(int32_t m, int32_t n, int32_t nnz,
+                           const int32_t *row_ptr, const int32_t *col_idx, const double *val,
+                           const double *x, double *y, const ssspmv_opts *opts, void *stream);
 
 /* The same product with HOST arrays (pageable or pinned): copies row_ptr,
  * col_idx, val and x into `dev_buffer` (device memory of at least

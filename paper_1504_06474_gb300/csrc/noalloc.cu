@@ -1,0 +1,72 @@
+// noalloc.cu -- ssspmv_csr_f64_noalloc: the FP64 product with its workspace in
+// a fixed device array owned by this library, for callers that cannot
+// allocate device memory themselves.
+//
+// Who needs it: code that is handed device pointers for A, x and y but owns no
+// allocator -- a plug-in called from inside another application's solver
+// loop, whose device memory belongs to the host application's pool -- and code
+// that must not call cudaMalloc/cudaFree on its hot path, because those calls
+// can synchronise the whole device and stall every other stream.
+//
+// Scratch rules: the array below holds the tile offsets, per-tile info and
+// synchronizer records of one call (SSSPMV_NOALLOC_SCRATCH_BYTES in total).
+// Every GPU that loads this library holds it until the process exits.  All
+// calls on a device share it and it keeps the last call's contents; the
+// kernels write every scratch entry they later read (the device error word
+// is cleared by the first kernel of each call), so nothing has to be zeroed
+// in between.  Calls whose kernels overlap on the GPU (different streams, no
+// ordering between them) race on the shared array and corrupt each other's
+// results: order them on one stream or through events.
+//
+// Set-up: the first call on a device looks up the array's device address with
+// cudaGetSymbolAddress while that device is current and caches it; make that
+// first call before any stream capture begins.  No call allocates device
+// memory (no cudaMalloc, cudaFree or allocating library routine).
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "ssspmv.h"
+
+namespace ssspmv {
+int record_cuda_error(cudaError_t e);  // api.cu
+}
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SSSPMV_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+void *g_scratch_addr[kMaxDevices] = {nullptr};
+
+}  // namespace
+
+extern "C" int ssspmv_csr_f64_noalloc(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr,
+                                      const int32_t *col_idx, const double *val, const double *x,
+                                      double *y, const ssspmv_opts *opts, void *stream)
+{
+    if (m < 0 || n < 0 || nnz < 0) return SSSPMV_EINVAL;
+    const size_t need = ssspmv_workspace_bytes(m, nnz, 8, opts);
+    if (need == 0) return SSSPMV_EINVAL;
+    if (need > (size_t)SSSPMV_NOALLOC_SCRATCH_BYTES) return SSSPMV_ETOOLARGE;
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return ssspmv::record_cuda_error(e);
+    if (dev < 0 || dev >= kMaxDevices) return SSSPMV_EINVAL;
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_mutex);
+        if (!g_scratch_addr[dev]) {
+            // host code only knows the array by a host-side stand-in; its
+            // device address is looked up once, with this device current
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return ssspmv::record_cuda_error(e);
+            g_scratch_addr[dev] = p;
+        }
+        scratch = g_scratch_addr[dev];
+    }
+    return ssspmv_csr_f64(m, n, nnz, row_ptr, col_idx, val, x, y, opts, scratch,
+                          (size_t)SSSPMV_NOALLOC_SCRATCH_BYTES, stream);
+}

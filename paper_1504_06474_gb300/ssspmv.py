@@ -24,6 +24,8 @@ SSSPMV_EWORKSPACE = -2
 SSSPMV_ECUDA = -3
 SSSPMV_EDEVICE = -4
 SSSPMV_EUNSUPPORTED = -5
+SSSPMV_ETOOLARGE = -6
+SSSPMV_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
 class SsspmvError(RuntimeError):
@@ -51,6 +53,7 @@ _SIGS = {
     "ssspmv_csr_f64": (ctypes.c_int, [i32, i32, i32, P, P, P, P, P, OPTS, P, sz, P]),
     "ssspmv_csr_f32": (ctypes.c_int, [i32, i32, i32, P, P, P, P, P, OPTS, P, sz, P]),
     "ssspmv_csr_bf16f32": (ctypes.c_int, [i32, i32, i32, P, P, P, P, P, OPTS, P, sz, P]),
+    "ssspmv_csr_f64_noalloc": (ctypes.c_int, [i32, i32, i32, P, P, P, P, P, OPTS, P]),
     "ssspmv_host_buffer_bytes": (sz, [i32, i32, i32, OPTS]),
     "ssspmv_csr_f64_host": (ctypes.c_int, [i32, i32, i32, P, P, P, P, P, OPTS, P, sz, P]),
     "ssspmv_csr_f64_debug": (ctypes.c_int, [i32, i32, i32, P, P, P, P, P, OPTS, P, sz, P,
@@ -175,6 +178,14 @@ def ssspmv_csr_bf16f32(m, n, nnz, row_ptr, col_idx, val, x, y, opts=None, worksp
     return _lib().ssspmv_csr_bf16f32(m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(val),
                                      _ptr(x), _ptr(y), _opts(opts), _ptr(workspace), ws_bytes,
                                      _stream(stream))
+
+
+def ssspmv_csr_f64_noalloc(m, n, nnz, row_ptr, col_idx, val, x, y, opts=None,
+                           stream=None) -> int:
+    """FP64 product with the library's fixed scratch instead of a workspace,
+    for callers that cannot allocate device memory (see include/ssspmv.h)."""
+    return _lib().ssspmv_csr_f64_noalloc(m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(val),
+                                         _ptr(x), _ptr(y), _opts(opts), _stream(stream))
 
 
 def ssspmv_host_buffer_bytes(m, n, nnz, opts=None) -> int:
