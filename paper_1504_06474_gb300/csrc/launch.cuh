@@ -90,7 +90,8 @@ int run_shape(const Call &c)
     if (c.ev && (e = cudaEventRecord(c.ev[0], c.stream)) != cudaSuccess)
         return record_cuda_error(e);
     {
-        launch_partition(c.row_ptr, c.m, c.nnz, l.L, l.ntiles, toff, err, c.stream);
+        launch_partition(c.row_ptr, c.m, c.nnz, l.L, l.ntiles, toff, err, c.stream,
+                         partition_method(c.m, l.ntiles));
     }
     if (c.ev && (e = cudaEventRecord(c.ev[1], c.stream)) != cudaSuccess)
         return record_cuda_error(e);
@@ -150,7 +151,10 @@ int run_shape(const Call &c)
         a.L = l.L;
         a.ntiles = l.ntiles;
         a.nbunches = l.nbunches;
-        a.nblk_tiles = (int32_t)((l.ntiles + kCalibWarps - 1) / kCalibWarps);
+        // warps of the tile role stride over the tiles (at most 16 per SM's worth)
+        int64_t tblk = (l.ntiles + kCalibWarps - 1) / kCalibWarps;
+        const int64_t tcap = (int64_t)device_sm_count() * 16;
+        a.nblk_tiles = (int32_t)(tblk < tcap ? tblk : tcap);
         a.nblk_sync = (int32_t)((l.nbunches + kCalibWarps - 1) / kCalibWarps);
         a.nblk_zero = kZeroBlocks;
         const unsigned grid = (unsigned)(a.nblk_tiles + a.nblk_sync + a.nblk_zero);

@@ -1,7 +1,9 @@
 // partition.cu -- kernel (a): tile boundaries on row_ptr (Sec. 3.2, Algorithm 1:
 // each boundary b_t = min(t*L, nnz) is binary-searched on row_ptr and the
 // rightmost match is kept, so a run of empty rows sharing the pointer b_t is
-// skipped and the tile starts at the row that holds entry b_t).
+// skipped and the tile starts at the row that holds entry b_t).  Two
+// launches compute the same array: the per-boundary binary search of the
+// paper, and a row-parallel scatter that streams row_ptr once.
 #include <cuda_runtime.h>
 
 #include "segsum.cuh"
@@ -29,9 +31,48 @@ __global__ void __launch_bounds__(kPartitionThreads)
     tile_offset[t] = lo;
 }
 
-void launch_partition(const int32_t *row_ptr, int32_t m, int32_t nnz, int32_t L, int64_t ntiles,
-                      int32_t *tile_offset, uint32_t *err, cudaStream_t stream)
+// The same partition computed from the rows' side in one streaming pass: the
+// boundary b_t < nnz lies in exactly one non-empty row r (row_ptr[r] <= b_t <
+// row_ptr[r+1]), which is the rightmost row with row_ptr[r] <= b_t; so each
+// non-empty row writes its index to the boundaries it contains.  Reads
+// row_ptr once, coalesced, instead of ~log2(m) dependent probes per boundary.
+__global__ void __launch_bounds__(kPartitionThreads)
+    partition_scatter_kernel(const int32_t *__restrict__ row_ptr, int32_t m, int32_t nnz,
+                             int32_t L, int64_t ntiles, int32_t *__restrict__ tile_offset,
+                             uint32_t *err)
 {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i0 == 0) {
+        *err = 0u;
+        tile_offset[ntiles] = m;  // b = nnz: every row pointer is <= nnz
+    }
+    for (int64_t r = i0; r < m; r += stride) {
+        const int32_t lo = __ldg(row_ptr + r), hi = __ldg(row_ptr + r + 1);
+        if (lo >= hi) continue;
+        // tiles t with lo <= t*L < hi
+        for (int64_t t = (lo + (int64_t)L - 1) / L; t * L < hi; ++t) tile_offset[t] = (int32_t)r;
+    }
+}
+
+int partition_method(int32_t m, int64_t ntiles)
+{
+    // the scatter reads m+1 row pointers once; the search issues ~log2(m)
+    // dependent probes per boundary
+    return (int64_t)m < 64 * (ntiles + 1) ? 1 : 0;
+}
+
+void launch_partition(const int32_t *row_ptr, int32_t m, int32_t nnz, int32_t L, int64_t ntiles,
+                      int32_t *tile_offset, uint32_t *err, cudaStream_t stream, int method)
+{
+    if (method == 1) {
+        int64_t blocks = ((int64_t)m + kPartitionThreads - 1) / kPartitionThreads;
+        if (blocks > 65536) blocks = 65536;
+        if (blocks < 1) blocks = 1;
+        partition_scatter_kernel<<<(unsigned)blocks, kPartitionThreads, 0, stream>>>(
+            row_ptr, m, nnz, L, ntiles, tile_offset, err);
+        return;
+    }
     const int64_t nthreads = ntiles + 1;
     const unsigned grid = (unsigned)((nthreads + kPartitionThreads - 1) / kPartitionThreads);
     partition_kernel<<<grid, kPartitionThreads, 0, stream>>>(row_ptr, m, nnz, L, ntiles,

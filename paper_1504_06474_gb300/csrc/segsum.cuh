@@ -108,8 +108,70 @@ using BF16C = CompF32Traits<__nv_bfloat16>;  // BF16 val, FP32 x, y
 // row_ptr, returning the rightmost match).  One thread per boundary.
 
 // Thread 0 also clears the workspace's device error word for this call.
+// method 0 = binary search per boundary, 1 = row-parallel scatter (same result).
 void launch_partition(const int32_t *row_ptr, int32_t m, int32_t nnz, int32_t L, int64_t ntiles,
-                      int32_t *tile_offset, uint32_t *err, cudaStream_t stream);
+                      int32_t *tile_offset, uint32_t *err, cudaStream_t stream, int method);
+// the method used when the caller does not choose (the cheaper one)
+int partition_method(int32_t m, int64_t ntiles);
+
+// ---------------------------------------------------------------------------
+// row-pointer searches used when a tile spans many (mostly empty) rows
+
+// first j in [lo, hi] with row_ptr[j] >= p, or hi + 1 if none
+__device__ __forceinline__ int32_t rp_lower_bound(const int32_t *__restrict__ row_ptr,
+                                                  int32_t lo, int32_t hi, int64_t p)
+{
+    int32_t a = lo, z = hi + 1;
+    while (a < z) {
+        const int32_t mid = a + ((z - a) >> 1);
+        if ((int64_t)__ldg(row_ptr + mid) < p) a = mid + 1;
+        else z = mid;
+    }
+    return a;
+}
+
+// last j in [lo, hi] with row_ptr[j] <= p (row_ptr[lo] <= p assumed)
+__device__ __forceinline__ int32_t rp_rightmost(const int32_t *__restrict__ row_ptr, int32_t lo,
+                                               int32_t hi, int64_t p)
+{
+    int32_t a = lo, z = hi;
+    while (a < z) {
+        const int32_t mid = a + ((z - a + 1) >> 1);
+        if ((int64_t)__ldg(row_ptr + mid) <= p) a = mid;
+        else z = mid - 1;
+    }
+    return a;
+}
+
+// Row starts inside tile positions [lo, hi) (absolute entry indices): calls
+// f(pos, r) for each distinct start position pos and the non-empty row r that
+// begins there (when need_row; r = -1 otherwise), among rows (start, stop].
+// O(heads * log(stop - start)) probes instead of a walk over every row.
+template <bool need_row, class F>
+__device__ __forceinline__ void for_row_starts(const int32_t *__restrict__ row_ptr, int32_t start,
+                                               int32_t stop, int64_t lo, int64_t hi, F &&f)
+{
+    int64_t p = lo;
+    int32_t jlo = start + 1;
+    while (p < hi && jlo <= stop) {
+        const int32_t j = rp_lower_bound(row_ptr, jlo, stop, p);
+        if (j > stop) break;
+        const int64_t v = __ldg(row_ptr + j);
+        if (v >= hi) break;
+        int32_t r = -1;
+        if (need_row) {
+            r = rp_rightmost(row_ptr, j, stop, v);
+            jlo = r + 1;
+        } else {
+            jlo = j + 1;
+        }
+        f(v, r);
+        p = v + 1;
+    }
+}
+
+// tiles spanning more rows than this use the searches above
+constexpr int32_t kScanRows = 63;
 
 // ---------------------------------------------------------------------------
 // shared-memory layout of one warp in kernel (b)
@@ -230,9 +292,16 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
 
     const int32_t rF = __ldg(a.tile_offset + t0);  // the bunch's first row
     int32_t start = rF;
+    int32_t stop = __ldg(a.tile_offset + t0 + 1);
+    // row_ptr[start .. start+31]: the first chunk of this tile's row pointers,
+    // loaded one tile ahead (rows past m read row_ptr[m])
+    int32_t pr_chunk = __ldg(row_ptr + (start + lane < a.m ? start + lane : a.m));
     A carry = P::zero();
     A F = P::zero(), G = P::zero();
     bool hasG = false;
+
+    constexpr int HA = (W + 1) / 2;  // each lane's run is two FMA chains:
+    constexpr int HB = W - HA;       // entries [0, HA) and [HA, W)
 
     for (int64_t t = t0; t < t1; ++t) {
         const int it = (int)(t - t0);
@@ -241,36 +310,13 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
         const int64_t b = t * L;
         const int32_t len = (int32_t)((nnz - b < L) ? nnz - b : L);
         const int64_t e = b + len;
-        const int32_t stop = __ldg(a.tile_offset + t + 1);
 
-        // ---- segment descriptor built on chip from row_ptr[start..stop]
-        // (Sec. 3.2: offsets of the covered row pointers from the boundary;
-        // every row start inside the tile, including row `stop`'s) and the
-        // empty-row ("dirty") test over [start, stop).
-        if (lane <= W) desc[lane] = 0u;
-        __syncwarp();
-        bool dirty = false, cont = false, raw0 = false;
-        for (int64_t r0 = start; r0 <= stop; r0 += 32) {
-            const int32_t r = (int32_t)(r0 + lane);
-            if (r0 + lane <= stop) {
-                const int32_t pr = __ldg(row_ptr + r);
-                const int64_t k = (int64_t)pr - b;
-                if (k >= 0 && k < len) atomicOr(&desc[k >> 5], 1u << (k & 31));
-                if (r < stop && __ldg(row_ptr + r + 1) == pr) dirty = true;
-                if (r == start && k == 0) raw0 = true;
-                if (r == stop && (int64_t)pr < e) cont = true;
-            }
+        // ---- prefetch the next tile's boundary row and first row-pointer chunk
+        int32_t stop_nx = 0, pr_nx = 0;
+        if (t + 1 < t1) {
+            stop_nx = __ldg(a.tile_offset + t + 2);
+            pr_nx = __ldg(row_ptr + (stop + lane < a.m ? stop + lane : a.m));
         }
-        dirty = __any_sync(FULL, dirty);
-        cont = __any_sync(FULL, cont);
-        raw0 = __any_sync(FULL, raw0);
-        __syncwarp();
-        const int bit0 = lane * W;
-        const uint64_t win =
-            ((uint64_t)desc[(bit0 >> 5) + 1] << 32) | (uint64_t)desc[bit0 >> 5];
-        uint32_t hb = (uint32_t)(win >> (bit0 & 31)) & ((1u << W) - 1u);
-        if (a.dbg_desc != nullptr && lane < W) a.dbg_desc[t * W + lane] = desc[lane];
-        if (lane == 0) hb |= 1u;  // each tile opens with a segment (Sec. 3.2)
 
         // ---- wait for this tile's val/col
         unsigned char *st = stage_ptr(s);
@@ -295,7 +341,8 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
             __syncwarp();
         }
 
-        // ---- gathers of x for the lane's W entries (Alg. 1 products)
+        // ---- gathers of x for the lane's W entries (Alg. 1 products), issued
+        // before the descriptor work so their latency overlaps it
         X xv[W];
 #pragma unroll
         for (int j = 0; j < W; ++j) {
@@ -303,8 +350,75 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
             xv[j] = (k < len) ? P::gather(x, cs[k], pol_keep) : X(0);
         }
 
+        // ---- segment descriptor built on chip from row_ptr[start..stop]
+        // (Sec. 3.2: offsets of the covered row pointers from the boundary;
+        // every row start inside the tile, including row `stop`'s) and the
+        // empty-row ("dirty") test over [start, stop).
+        if (lane <= W) desc[lane] = 0u;
+        __syncwarp();
+        bool dirty = false, cont = false, raw0 = false;
+        const bool many_rows = stop - start > kScanRows;
+        if (!many_rows) {
+            {
+                const int32_t r = start + lane;
+                const int32_t pr = pr_chunk;
+                int32_t nx = __shfl_down_sync(FULL, pr, 1);
+                if (lane == 31 && r < stop) nx = __ldg(row_ptr + r + 1);
+                if (r <= stop) {
+                    const int64_t k = (int64_t)pr - b;
+                    if (k >= 0 && k < len) atomicOr(&desc[k >> 5], 1u << (k & 31));
+                    if (r < stop && nx == pr) dirty = true;
+                    if (lane == 0 && k == 0) raw0 = true;
+                    if (r == stop && (int64_t)pr < e) cont = true;
+                }
+            }
+            if (start + 32 <= stop) {  // second chunk
+                const int32_t r = start + 32 + lane;
+                if (r <= stop) {
+                    const int32_t pr = __ldg(row_ptr + r);
+                    const int64_t k = (int64_t)pr - b;
+                    if (k >= 0 && k < len) atomicOr(&desc[k >> 5], 1u << (k & 31));
+                    if (r < stop && __ldg(row_ptr + r + 1) == pr) dirty = true;
+                    if (r == stop && (int64_t)pr < e) cont = true;
+                }
+            }
+        } else {
+            // many (mostly empty) rows: each lane searches the row starts in
+            // its own W positions; dirty follows from the head count below
+            if (lane == 0) {
+                raw0 = (int64_t)pr_chunk == b;
+                cont = stop < a.m && (int64_t)__ldg(row_ptr + stop) < e;
+                if (raw0) atomicOr(&desc[0], 1u);
+            }
+            const int64_t lo = b + (int64_t)lane * W;
+            const int64_t hi = (lo + W < e) ? lo + W : e;
+            for_row_starts<false>(row_ptr, start, stop, lo, hi, [&](int64_t v, int32_t) {
+                const int64_t k = v - b;
+                atomicOr(&desc[k >> 5], 1u << (k & 31));
+            });
+        }
+        dirty = __any_sync(FULL, dirty);
+        cont = __any_sync(FULL, cont);
+        raw0 = __any_sync(FULL, raw0);
+        __syncwarp();
+        const int bit0 = lane * W;
+        const uint64_t win =
+            ((uint64_t)desc[(bit0 >> 5) + 1] << 32) | (uint64_t)desc[bit0 >> 5];
+        uint32_t hb = (uint32_t)(win >> (bit0 & 31)) & ((1u << W) - 1u);
+        if (many_rows) {
+            // rows in [start, stop) minus non-empty ones: the non-empty rows
+            // there are row `start` plus one per row start inside the tile,
+            // except row `stop`'s own start when it continues
+            const int heads = __reduce_add_sync(FULL, (unsigned)__popc(lane == 0 ? hb & ~1u : hb));
+            dirty = (int64_t)(stop - start) > 1 + (int64_t)heads - (cont ? 1 : 0);
+        }
+        if (a.dbg_desc != nullptr && lane < W) a.dbg_desc[t * W + lane] = desc[lane];
+        if (lane == 0) hb |= 1u;  // each tile opens with a segment (Sec. 3.2)
+
         // ---- compact indices: exclusive scan of head counts (Alg. 1 y_index)
-        const int c = __popc(hb);
+        const uint32_t hbA = hb & ((1u << HA) - 1u), hbB = hb >> HA;
+        const int cA = __popc(hbA), cB = __popc(hbB);
+        const int c = cA + cB;
         const int incl = warp_inclusive_scan(c, lane);
         const int idx0 = incl - c;
         const int nseg = __shfl_sync(FULL, incl, 31);
@@ -320,25 +434,40 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
             }
         };
 
-        // ---- per-lane sequential segmented sum: one FMA per entry; a head
-        // closes the open segment (the part before the lane's first head
-        // belongs to a segment opened in an earlier lane)
-        A acc = P::zero(), pre = P::zero();
-        int cur = idx0 - 1;
+        // ---- per-lane sequential segmented sum, one FMA per entry, as two
+        // interleaved chains; a head closes the open segment (the part before
+        // a chain's first head belongs to a segment opened earlier)
+        A accA = P::zero(), preA = P::zero(), accB = P::zero(), preB = P::zero();
+        int curA = idx0 - 1, curB = idx0 + cA - 1;
 #pragma unroll
-        for (int j = 0; j < W; ++j) {
-            const int k = lane * W + j;
-            if ((hb >> j) & 1u) {
-                if (cur >= idx0) emit(cur, acc);
-                else pre = acc;
-                ++cur;
-                acc = (j == 0 && lane == 0) ? cin : P::zero();
+        for (int i = 0; i < HA; ++i) {
+            const int kA = lane * W + i;
+            if ((hbA >> i) & 1u) {
+                if (curA >= idx0) emit(curA, accA);
+                else preA = accA;
+                ++curA;
+                accA = (i == 0 && lane == 0) ? cin : P::zero();
             }
-            if (k < len) acc = P::fma(vs[k], xv[j], acc);
+            if (kA < len) accA = P::fma(vs[kA], xv[i], accA);
+            if (i < HB) {
+                const int kB = lane * W + HA + i;
+                if ((hbB >> i) & 1u) {
+                    if (curB >= idx0 + cA) emit(curB, accB);
+                    else preB = accB;
+                    ++curB;
+                    accB = P::zero();
+                }
+                if (kB < len) accB = P::fma(vs[kB], xv[HA + i], accB);
+            }
         }
+        if (cA == 0) preA = accA;  // chain totals when a chain has no head
+        if (cB == 0) preB = accB;
+        // join the chains with one add: A's open part + B's leading part
+        const A join = P::add(accA, preB);
+        if (cA > 0 && cB > 0) emit(idx0 + cA - 1, join);
+        const A pre = (cA > 0) ? preA : join;   // the lane's part before its first head
+        const A v = (cB > 0) ? accB : join;     // suffix if the lane has a head, else total
         const bool has = c > 0;
-        if (!has) pre = acc;
-        const A v = acc;  // suffix (open segment) if has, else the lane total
 
         // ---- cross-lane segmented sum of the open segments:
         // C_l = sum of v over lanes first_l..l, first_l = last lane <= l with
@@ -380,12 +509,14 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
         if (lane == 0) a.tile_info[t] = (uint32_t)nseg | (dirty ? 0x80000000u : 0u);
         __syncwarp();
         carry = *slot_carry;
-        // ---- release the stage: copy the tile S+STAGES ahead into it
+        // ---- release the stage: copy the tile STAGES ahead into it
         if (lane == 0 && t + STAGES < t1) {
             fence_proxy_async_smem();
             issue(t + STAGES, s);
         }
         start = stop;
+        stop = stop_nx;
+        pr_chunk = pr_nx;
     }
     __syncwarp();
     F = *slot_f;
@@ -426,33 +557,29 @@ struct CalibArgs {
 
 constexpr int kCalibWarps = 8;
 
+// re-arrangement of one dirty tile by a warp: the s-th partial (s >= 1,
+// speculatively at y[start+s]) moves to the s-th non-empty row inside
+// (start, stop); the other rows there become 0.
 template <class P>
-__global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const CalibArgs a)
+__device__ __forceinline__ void repair_dirty_tile(const CalibArgs &a, int64_t t, uint32_t info,
+                                                  int lane)
 {
     using Y = typename P::y_t;
-    using A = typename P::acc_t;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
+    constexpr int kMaxHeadsPerLane = 32;
     Y *__restrict__ y = static_cast<Y *>(a.y);
     const int32_t *__restrict__ row_ptr = a.row_ptr;
-    int blk = blockIdx.x;
-
-    if (blk < a.nblk_tiles) {
-        // ---- re-arrangement of a dirty tile (Sec. 3.2, checking prediction)
-        const int64_t t = (int64_t)blk * kCalibWarps + warp;
-        if (t >= a.ntiles) return;
-        const uint32_t info = __ldg(a.tile_info + t);
-        if (!(info >> 31)) return;
-        const int32_t nseg = (int32_t)(info & 0x7fffffffu);
-        const int32_t start = __ldg(a.tile_offset + t);
-        const int32_t stop = __ldg(a.tile_offset + t + 1);
-        const int64_t e = (t + 1) * (int64_t)a.L < a.nnz ? (t + 1) * (int64_t)a.L : a.nnz;
-        const bool cont = stop < a.m && (int64_t)__ldg(row_ptr + stop) < e;
-        // non-empty rows strictly inside (start, stop): each holds one segment
-        const int32_t K = nseg - 1 - (cont ? 1 : 0);
+    const int32_t nseg = (int32_t)(info & 0x7fffffffu);
+    const int32_t start = __ldg(a.tile_offset + t);
+    const int32_t stop = __ldg(a.tile_offset + t + 1);
+    const int64_t b = t * (int64_t)a.L;
+    const int64_t e = b + a.L < a.nnz ? b + a.L : a.nnz;
+    const bool cont = stop < a.m && (int64_t)__ldg(row_ptr + stop) < e;
+    // non-empty rows strictly inside (start, stop): each holds one segment
+    const int32_t K = nseg - 1 - (cont ? 1 : 0);
+    if (stop - start <= kScanRows + 1 || a.L > 32 * kMaxHeadsPerLane) {
+        // short range: walk down from stop-1 so that every slot is read before
+        // any write can reach it (the s-th partial moves from start+s up)
         int32_t above = 0;
-        // walk down from stop-1 so that every slot is read before any write
-        // can reach it (the s-th partial moves from start+s up to its row)
         for (int32_t hi = stop - 1; hi > start; hi -= 32) {
             const int32_t r = hi - lane;
             const bool valid = r > start;
@@ -471,6 +598,52 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
             __syncwarp();
         }
         if (lane == 0 && above != K) atomicOr(a.err, SSSPMV_DEV_CALIB);
+        return;
+    }
+    // long range: find the row starts inside the tile by searches (each lane
+    // its own W positions), read every moving partial, zero the whole range,
+    // then store the partials in their rows
+    const int32_t Wl = a.L / 32;
+    const int64_t lo = b + (int64_t)lane * Wl;
+    const int64_t hi = (lo + Wl < e) ? lo + Wl : e;
+    int32_t rows[kMaxHeadsPerLane];
+    int nh = 0;
+    for_row_starts<true>(row_ptr, start, stop, lo, hi, [&](int64_t, int32_t r) {
+        if (r < stop && nh < kMaxHeadsPerLane) rows[nh++] = r;
+    });
+    const int incl = warp_inclusive_scan(nh, lane);
+    const int first_s = incl - nh + 1;  // segment index of the lane's first head
+    if (lane == 31 && incl != K) atomicOr(a.err, SSSPMV_DEV_CALIB);
+    Y vals[kMaxHeadsPerLane];
+#pragma unroll
+    for (int i = 0; i < kMaxHeadsPerLane; ++i)
+        if (i < nh) vals[i] = y[start + first_s + i];
+    __syncwarp();
+    for (int64_t r = (int64_t)start + 1 + lane; r < stop; r += 32) y[r] = Y(0);
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < kMaxHeadsPerLane; ++i)
+        if (i < nh) y[rows[i]] = vals[i];
+}
+
+template <class P>
+__global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const CalibArgs a)
+{
+    using Y = typename P::y_t;
+    using A = typename P::acc_t;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    Y *__restrict__ y = static_cast<Y *>(a.y);
+    int blk = blockIdx.x;
+
+    if (blk < a.nblk_tiles) {
+        // ---- re-arrangement of dirty tiles (Sec. 3.2, checking prediction):
+        // the warps of this role stride over the tiles
+        const int64_t nw = (int64_t)a.nblk_tiles * kCalibWarps;
+        for (int64_t t = (int64_t)blk * kCalibWarps + warp; t < a.ntiles; t += nw) {
+            const uint32_t info = __ldg(a.tile_info + t);
+            if (info >> 31) repair_dirty_tile<P>(a, t, info, lane);
+        }
         return;
     }
     blk -= a.nblk_tiles;
