@@ -108,6 +108,9 @@ def test_random_structures(dev, seed, mean, p_empty, p_long, long_len):
     [27] * 1000 + [0] + [27] * 1000,            # lanes aligned with rows, one empty
     [961, 0, 0, 961, 1],                        # rows exactly one tile long (W=31)
     [0] * 5 + [405] * 3 + [0] * 2 + [405],      # rows aligned with 15-wide tiles
+    [3] + [0] * 500 + [4] + [0] * 100 + [2] * 3 + [0] * 70,   # tiles over hundreds of rows
+    ([0] * 40 + [1]) * 60 + [0] * 3000,         # sparse rows, long empty tail
+    [500] + [0] * 2000 + [1] * 40 + [0] * 90 + [700],       # long rows around empty runs
 ])
 def test_edge_structures(dev, lens):
     A = synth.from_lengths(lens, 64, seed=len(lens))
@@ -115,6 +118,25 @@ def test_edge_structures(dev, lens):
     for W in _api()[1].ssspmv_supported_w():
         for S in (0, 1, 2):
             check_case(dev, A.row_ptr, A.col, A.val, x, A.n, W=W, S=S)
+
+
+@pytest.mark.parametrize("scale,inject", [(12, 0), (14, 3000), (16, 50000)])
+def test_small_rmat(dev, scale, inject):
+    """R-MAT's sparse tail: tiles spanning thousands of mostly empty rows."""
+    A = synth.rmat(scale, 16, seed=scale, inject_len=inject)
+    x = synth.sym_vector(A.n, seed=scale + 1)
+    for W in (15, 27):
+        for S in (0, 1, 5):
+            check_case(dev, A.row_ptr, A.col, A.val, x, A.n, W=W, S=S)
+
+
+def test_sparse_random(dev):
+    lens = synth.random_lengths(60000, seed=13, mean=30, p_empty=0.95)
+    A = synth.from_lengths(lens, 8000, seed=13)
+    x = synth.sym_vector(8000, seed=14)
+    for W in (15, 21, 31):
+        check_case(dev, A.row_ptr, A.col, A.val, x, A.n, W=W, S=0)
+        check_case(dev, A.row_ptr, A.col, A.val, x, A.n, W=W, S=2)
 
 
 def test_duplicates_and_unsorted_columns(dev):
