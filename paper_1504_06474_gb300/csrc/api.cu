@@ -106,12 +106,8 @@ static int make_layout(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_o
     l.W = W;
     l.L = 32 * W;
     l.ntiles = ((int64_t)nnz + l.L - 1) / l.L;
-    const int32_t S_opt = o ? o->S : 0;
-    if (S_opt > 0) {
-        l.nbunch_cap = (l.ntiles + S_opt - 1) / S_opt;
-    } else {
-        l.nbunch_cap = l.ntiles < kMaxAutoBunches ? l.ntiles : kMaxAutoBunches;
-    }
+    const int32_t S = (o && o->S > 0) ? o->S : kDefaultS;
+    l.nbunch_cap = (l.ntiles + S - 1) / S;
     carve(l);
     return SSSPMV_OK;
 }

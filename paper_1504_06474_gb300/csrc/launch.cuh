@@ -51,23 +51,11 @@ int segsum_resident_warps()
     return cache[dev];
 }
 
-// choose S (tiles per bunch) and the bunch count for this call
+// S (tiles per bunch) and the bunch count for this call
 template <class P, int W>
 void resolve_bunches(Layout &l, int32_t S_opt)
 {
-    if (l.ntiles == 0) {
-        l.S = S_opt > 0 ? S_opt : 1;
-        l.nbunches = 0;
-        return;
-    }
-    if (S_opt > 0) {
-        l.S = S_opt;
-    } else {
-        int64_t total = (int64_t)device_sm_count() * segsum_resident_warps<P, W>();
-        if (total > kMaxAutoBunches) total = kMaxAutoBunches;
-        if (total < 1) total = 1;
-        l.S = (int32_t)((l.ntiles + total - 1) / total);
-    }
+    l.S = S_opt > 0 ? S_opt : kDefaultS;
     l.nbunches = (l.ntiles + l.S - 1) / l.S;
 }
 
@@ -109,6 +97,7 @@ int run_shape(const Call &c)
         a.tail_val = tval;
         a.tail_flag = tflag;
         a.err = err;
+        a.ticket = err + 1;
         a.dbg_desc = c.dbg_desc;
         a.m = c.m;
         a.nnz = c.nnz;
@@ -125,7 +114,11 @@ int run_shape(const Call &c)
             if (e != cudaSuccess) return record_cuda_error(e);
             attr_done[dev] = 1;
         }
-        const unsigned grid = (unsigned)((l.nbunches + B - 1) / B);
+        // one wave of persistent warps; bunches beyond it come from the ticket
+        int64_t nw = (int64_t)device_sm_count() * segsum_resident_warps<P, W>();
+        if (nw > l.nbunches) nw = l.nbunches;
+        if (nw < 1) nw = 1;
+        const unsigned grid = (unsigned)((nw + B - 1) / B);
         kb<<<grid, B * 32, B * SM::BYTES, c.stream>>>(a);
     }
     if (c.dbg_yspec && c.m > 0) {
@@ -155,7 +148,7 @@ int run_shape(const Call &c)
         int64_t tblk = (l.ntiles + kCalibWarps - 1) / kCalibWarps;
         const int64_t tcap = (int64_t)device_sm_count() * 16;
         a.nblk_tiles = (int32_t)(tblk < tcap ? tblk : tcap);
-        a.nblk_sync = (int32_t)((l.nbunches + kCalibWarps - 1) / kCalibWarps);
+        a.nblk_sync = (int32_t)((l.nbunches + 32 * kCalibWarps - 1) / (32 * kCalibWarps));
         a.nblk_zero = kZeroBlocks;
         const unsigned grid = (unsigned)(a.nblk_tiles + a.nblk_sync + a.nblk_zero);
         calibrate_kernel<P><<<grid, kCalibWarps * 32, 0, c.stream>>>(a);

@@ -7,9 +7,9 @@
 
 namespace ssspmv {
 
-// upper bound on resident warps of any launch (sizes the synchronizer when S
-// is chosen automatically, keeping the workspace size device independent)
-constexpr int64_t kMaxAutoBunches = 16384;
+// tiles per thread-bunch when the caller does not choose S: small bunches,
+// handed out dynamically, balance tiles that differ in cost (many empty rows)
+constexpr int32_t kDefaultS = 4;
 
 struct Layout {
     int32_t W = 0, L = 0, S = 0;

@@ -10,6 +10,8 @@
 
 namespace ssspmv {
 
+int device_sm_count();  // api.cu
+
 constexpr int kPartitionThreads = 256;
 
 __global__ void __launch_bounds__(kPartitionThreads)
@@ -17,7 +19,10 @@ __global__ void __launch_bounds__(kPartitionThreads)
                      int64_t ntiles, int32_t *__restrict__ tile_offset, uint32_t *err)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t == 0) *err = 0u;
+    if (t == 0) {
+        err[0] = 0u;  // device error word
+        err[1] = 0u;  // bunch ticket of kernel (b)
+    }
     if (t > ntiles) return;
     const int64_t bl = t * (int64_t)L;
     const int32_t b = (int32_t)(bl < nnz ? bl : nnz);
@@ -44,14 +49,24 @@ __global__ void __launch_bounds__(kPartitionThreads)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i0 == 0) {
-        *err = 0u;
+        err[0] = 0u;  // device error word
+        err[1] = 0u;  // bunch ticket of kernel (b)
         tile_offset[ntiles] = m;  // b = nnz: every row pointer is <= nnz
     }
-    for (int64_t r = i0; r < m; r += stride) {
-        const int32_t lo = __ldg(row_ptr + r), hi = __ldg(row_ptr + r + 1);
-        if (lo >= hi) continue;
-        // tiles t with lo <= t*L < hi
-        for (int64_t t = (lo + (int64_t)L - 1) / L; t * L < hi; ++t) tile_offset[t] = (int32_t)r;
+    for (int64_t r0 = i0; r0 < m; r0 += 4 * stride) {
+        int32_t lo[4], hi[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {  // four independent rows in flight
+            const int64_t r = r0 + u * stride;
+            lo[u] = r < m ? __ldg(row_ptr + r) : 0;
+            hi[u] = r < m ? __ldg(row_ptr + r + 1) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            // tiles t with lo <= t*L < hi
+            for (int64_t t = (lo[u] + (int64_t)L - 1) / L; t * L < hi[u]; ++t)
+                tile_offset[t] = (int32_t)(r0 + u * stride);
+        }
     }
 }
 
@@ -67,7 +82,8 @@ void launch_partition(const int32_t *row_ptr, int32_t m, int32_t nnz, int32_t L,
 {
     if (method == 1) {
         int64_t blocks = ((int64_t)m + kPartitionThreads - 1) / kPartitionThreads;
-        if (blocks > 65536) blocks = 65536;
+        const int64_t cap = 8LL * device_sm_count();
+        if (blocks > cap) blocks = cap;
         if (blocks < 1) blocks = 1;
         partition_scatter_kernel<<<(unsigned)blocks, kPartitionThreads, 0, stream>>>(
             row_ptr, m, nnz, L, ntiles, tile_offset, err);

@@ -221,6 +221,7 @@ struct SegsumArgs {
     void *tail_val;
     int32_t *tail_flag;
     uint32_t *err;
+    uint32_t *ticket;    // bunch ticket counter, zero at launch
     uint32_t *dbg_desc;  // nullable
     int32_t m;
     int32_t nnz;
@@ -230,7 +231,12 @@ struct SegsumArgs {
 };
 
 // ---------------------------------------------------------------------------
-// kernel (b): one warp = one thread-bunch over S consecutive tiles
+// kernel (b): a thread-bunch (warp) processes S consecutive tiles, carrying the
+// transmitter from tile to tile.  Bunches are handed to a persistent grid of
+// warps: warp g starts with bunch g, then takes the next unclaimed bunch from
+// a ticket counter -- the dynamic assignment of the paper's thread-groups to
+// cores, without refilling the copy pipeline at every bunch (the copies of a
+// warp's next bunch are issued while it finishes the current one).
 
 template <class P, int W, int B>
 __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
@@ -250,14 +256,12 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
     unsigned char *base = smem_raw + warp * SM::BYTES;
     uint64_t *bar = reinterpret_cast<uint64_t *>(base + SM::BAR_OFF);
     uint32_t *desc = reinterpret_cast<uint32_t *>(base + SM::DESC_OFF);
-    A *slot_f = reinterpret_cast<A *>(base + SM::SLOT_OFF);       // bunch-first partial
+    A *slot_f = reinterpret_cast<A *>(base + SM::SLOT_OFF);           // bunch-first partial
     A *slot_carry = reinterpret_cast<A *>(base + SM::SLOT_OFF + 16);  // transmitter
 
-    const int64_t w = (int64_t)blockIdx.x * B + warp;
-    if (w >= a.nbunches) return;
-    const int64_t t0 = w * a.S;
-    const int64_t t1 = (t0 + a.S < a.ntiles) ? t0 + a.S : a.ntiles;
-    if (t0 >= t1) return;
+    const int64_t nwarps = (int64_t)gridDim.x * B;
+    int64_t cur = (int64_t)blockIdx.x * B + warp;  // bunch being processed
+    if (cur >= a.nbunches) return;
 
     const V *__restrict__ val = static_cast<const V *>(a.val);
     const X *__restrict__ x = static_cast<const X *>(a.x);
@@ -265,13 +269,23 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
     const int32_t *__restrict__ row_ptr = a.row_ptr;
     const int32_t *__restrict__ col = a.col;
     const int32_t nnz = a.nnz;
+    const int64_t S = a.S;
 
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
 
-    auto stage_ptr = [&](int s) { return base + s * SM::STAGE_BYTES; };
-    // issue the bulk copies of tile tt into stage s (lane 0 only)
-    auto issue = [&](int64_t tt, int s) {
+    auto bunch_end = [&](int64_t bb) { return (bb * S + S < a.ntiles) ? bb * S + S : a.ntiles; };
+    int64_t nxt = -1;  // the warp's next bunch, once claimed (warp-uniform)
+    auto claim_next = [&]() {
+        if (nxt >= 0) return;
+        uint32_t v = 0;
+        if (lane == 0) v = atomicAdd(a.ticket, 1u);
+        nxt = nwarps + (int64_t)__shfl_sync(FULL, v, 0);
+    };
+
+    auto stage_ptr = [&](uint32_t s) { return base + s * SM::STAGE_BYTES; };
+    // bulk copies of tile tt into stage s (lane 0 only)
+    auto issue = [&](int64_t tt, uint32_t s) {
         const int64_t b = tt * L;
         const int32_t len = (int32_t)((nnz - b < L) ? nnz - b : L);
         const uint32_t vb = ((uint32_t)len * (uint32_t)sizeof(V)) & ~15u;
@@ -280,252 +294,285 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
         if (vb) bulk_g2s(stage_ptr(s), val + b, vb, &bar[s], pol_stream);
         if (cb) bulk_g2s(stage_ptr(s) + SM::VAL_REGION, col + b, cb, &bar[s], pol_stream);
     };
+    // the copy stream runs at most STAGES tiles ahead, into at most the next
+    // bunch (warp-uniform: every lane calls it)
+    int64_t iss_b = cur, iss_t = cur * S;
+    uint32_t q_iss = 0, q_con = 0;  // tiles issued / consumed by this warp
+    auto issue_next = [&]() {
+        if (iss_b >= a.nbunches) return;
+        if (iss_t >= bunch_end(iss_b)) {
+            if (iss_b != cur) return;
+            claim_next();
+            iss_b = nxt;
+            iss_t = nxt * S;
+            if (iss_b >= a.nbunches) return;
+        }
+        if (lane == 0) {
+            fence_proxy_async_smem();
+            issue(iss_t, q_iss % STAGES);
+        }
+        ++q_iss;
+        ++iss_t;
+    };
 
     if (lane == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
         fence_mbar_init();
     }
     __syncwarp();
-    if (lane == 0) {
-        for (int s = 0; s < STAGES && t0 + s < t1; ++s) issue(t0 + s, s);
-    }
+    for (int s = 0; s < STAGES; ++s) issue_next();
 
-    const int32_t rF = __ldg(a.tile_offset + t0);  // the bunch's first row
-    int32_t start = rF;
-    int32_t stop = __ldg(a.tile_offset + t0 + 1);
-    // row_ptr[start .. start+31]: the first chunk of this tile's row pointers,
-    // loaded one tile ahead (rows past m read row_ptr[m])
+    // boundary rows and the first row-pointer chunk of the next tile, loaded
+    // one tile ahead (rows past m read row_ptr[m])
+    int32_t start = __ldg(a.tile_offset + cur * S);
+    int32_t stop = __ldg(a.tile_offset + cur * S + 1);
     int32_t pr_chunk = __ldg(row_ptr + (start + lane < a.m ? start + lane : a.m));
-    A carry = P::zero();
-    A F = P::zero(), G = P::zero();
-    bool hasG = false;
 
     constexpr int HA = (W + 1) / 2;  // each lane's run is two FMA chains:
     constexpr int HB = W - HA;       // entries [0, HA) and [HA, W)
 
-    for (int64_t t = t0; t < t1; ++t) {
-        const int it = (int)(t - t0);
-        const int s = it % STAGES;
-        const uint32_t par = (uint32_t)((it / STAGES) & 1);
-        const int64_t b = t * L;
-        const int32_t len = (int32_t)((nnz - b < L) ? nnz - b : L);
-        const int64_t e = b + len;
+    while (true) {
+        const int64_t t0 = cur * S, t1 = bunch_end(cur);
+        const int32_t rF = start;  // the bunch's first row
+        A carry = P::zero();
+        A G = P::zero();
+        bool hasG = false;
 
-        // ---- prefetch the next tile's boundary row and first row-pointer chunk
-        int32_t stop_nx = 0, pr_nx = 0;
-        if (t + 1 < t1) {
-            stop_nx = __ldg(a.tile_offset + t + 2);
-            pr_nx = __ldg(row_ptr + (stop + lane < a.m ? stop + lane : a.m));
-        }
+        for (int64_t t = t0; t < t1; ++t) {
+            const uint32_t s = q_con % STAGES;
+            const uint32_t par = (q_con / STAGES) & 1u;
+            const int64_t b = t * L;
+            const int32_t len = (int32_t)((nnz - b < L) ? nnz - b : L);
+            const int64_t e = b + len;
 
-        // ---- wait for this tile's val/col
-        unsigned char *st = stage_ptr(s);
-        const V *vs = reinterpret_cast<const V *>(st);
-        const int32_t *cs = reinterpret_cast<const int32_t *>(st + SM::VAL_REGION);
-        if (!mbar_wait_bounded(&bar[s], par)) {
-            if (lane == 0) atomicOr(a.err, SSSPMV_DEV_TIMEOUT);
-            // drain the copies still in flight before leaving
-            for (int64_t tt = t; tt < t + STAGES && tt < t1; ++tt) {
-                const int jt = (int)(tt - t0);
-                mbar_wait_bounded(&bar[jt % STAGES], (uint32_t)((jt / STAGES) & 1));
+            // ---- prefetch the next tile's rows (the next bunch's first tile
+            // after the last one)
+            int32_t start_nx = stop, stop_nx = 0, pr_nx = 0;
+            bool have_nx = true;
+            if (t + 1 < t1) {
+                stop_nx = __ldg(a.tile_offset + t + 2);
+            } else {
+                claim_next();
+                if (nxt < a.nbunches) {
+                    start_nx = __ldg(a.tile_offset + nxt * S);
+                    stop_nx = __ldg(a.tile_offset + nxt * S + 1);
+                } else {
+                    have_nx = false;
+                }
             }
-            return;
-        }
-        if (len < L) {  // ragged last tile: the bulk copies stop at 16-byte multiples
-            V *vw = reinterpret_cast<V *>(st);
-            int32_t *cw = reinterpret_cast<int32_t *>(st + SM::VAL_REGION);
-            const int32_t vdone = (int32_t)((((uint32_t)len * (uint32_t)sizeof(V)) & ~15u) / sizeof(V));
-            const int32_t cdone = (int32_t)((((uint32_t)len * 4u) & ~15u) / 4u);
-            for (int32_t k = vdone + lane; k < len; k += 32) vw[k] = val[b + k];
-            for (int32_t k = cdone + lane; k < len; k += 32) cw[k] = col[b + k];
+            if (have_nx) pr_nx = __ldg(row_ptr + (start_nx + lane < a.m ? start_nx + lane : a.m));
+
+            // ---- wait for this tile's val/col
+            unsigned char *st = stage_ptr(s);
+            const V *vs = reinterpret_cast<const V *>(st);
+            const int32_t *cs = reinterpret_cast<const int32_t *>(st + SM::VAL_REGION);
+            if (!mbar_wait_bounded(&bar[s], par)) {
+                if (lane == 0) atomicOr(a.err, SSSPMV_DEV_TIMEOUT);
+                // drain the copies still in flight before leaving
+                for (uint32_t q = q_con; q < q_iss; ++q)
+                    mbar_wait_bounded(&bar[q % STAGES], (q / STAGES) & 1u);
+                return;
+            }
+            if (len < L) {  // ragged last tile: the bulk copies stop at 16-byte multiples
+                V *vw = reinterpret_cast<V *>(st);
+                int32_t *cw = reinterpret_cast<int32_t *>(st + SM::VAL_REGION);
+                const int32_t vdone =
+                    (int32_t)((((uint32_t)len * (uint32_t)sizeof(V)) & ~15u) / sizeof(V));
+                const int32_t cdone = (int32_t)((((uint32_t)len * 4u) & ~15u) / 4u);
+                for (int32_t k = vdone + lane; k < len; k += 32) vw[k] = val[b + k];
+                for (int32_t k = cdone + lane; k < len; k += 32) cw[k] = col[b + k];
+                __syncwarp();
+            }
+
+            // ---- gathers of x for the lane's W entries (Alg. 1 products),
+            // issued before the descriptor work so their latency overlaps it
+            X xv[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                const int k = lane * W + j;
+                xv[j] = (k < len) ? P::gather(x, cs[k], pol_keep) : X(0);
+            }
+
+            // ---- segment descriptor built on chip from row_ptr[start..stop]
+            // (Sec. 3.2: offsets of the covered row pointers from the
+            // boundary; every row start inside the tile, including row
+            // `stop`'s) and the empty-row ("dirty") test over [start, stop)
+            if (lane <= W) desc[lane] = 0u;
             __syncwarp();
-        }
-
-        // ---- gathers of x for the lane's W entries (Alg. 1 products), issued
-        // before the descriptor work so their latency overlaps it
-        X xv[W];
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
-            const int k = lane * W + j;
-            xv[j] = (k < len) ? P::gather(x, cs[k], pol_keep) : X(0);
-        }
-
-        // ---- segment descriptor built on chip from row_ptr[start..stop]
-        // (Sec. 3.2: offsets of the covered row pointers from the boundary;
-        // every row start inside the tile, including row `stop`'s) and the
-        // empty-row ("dirty") test over [start, stop).
-        if (lane <= W) desc[lane] = 0u;
-        __syncwarp();
-        bool dirty = false, cont = false, raw0 = false;
-        const bool many_rows = stop - start > kScanRows;
-        if (!many_rows) {
-            {
-                const int32_t r = start + lane;
-                const int32_t pr = pr_chunk;
-                int32_t nx = __shfl_down_sync(FULL, pr, 1);
-                if (lane == 31 && r < stop) nx = __ldg(row_ptr + r + 1);
-                if (r <= stop) {
-                    const int64_t k = (int64_t)pr - b;
-                    if (k >= 0 && k < len) atomicOr(&desc[k >> 5], 1u << (k & 31));
-                    if (r < stop && nx == pr) dirty = true;
-                    if (lane == 0 && k == 0) raw0 = true;
-                    if (r == stop && (int64_t)pr < e) cont = true;
+            bool dirty = false, cont = false, raw0 = false;
+            const bool many_rows = stop - start > kScanRows;
+            if (!many_rows) {
+                {
+                    const int32_t r = start + lane;
+                    const int32_t pr = pr_chunk;
+                    int32_t nx = __shfl_down_sync(FULL, pr, 1);
+                    if (lane == 31 && r < stop) nx = __ldg(row_ptr + r + 1);
+                    if (r <= stop) {
+                        const int64_t k = (int64_t)pr - b;
+                        if (k >= 0 && k < len) atomicOr(&desc[k >> 5], 1u << (k & 31));
+                        if (r < stop && nx == pr) dirty = true;
+                        if (lane == 0 && k == 0) raw0 = true;
+                        if (r == stop && (int64_t)pr < e) cont = true;
+                    }
                 }
-            }
-            if (start + 32 <= stop) {  // second chunk
-                const int32_t r = start + 32 + lane;
-                if (r <= stop) {
-                    const int32_t pr = __ldg(row_ptr + r);
-                    const int64_t k = (int64_t)pr - b;
-                    if (k >= 0 && k < len) atomicOr(&desc[k >> 5], 1u << (k & 31));
-                    if (r < stop && __ldg(row_ptr + r + 1) == pr) dirty = true;
-                    if (r == stop && (int64_t)pr < e) cont = true;
+                if (start + 32 <= stop) {  // second chunk
+                    const int32_t r = start + 32 + lane;
+                    if (r <= stop) {
+                        const int32_t pr = __ldg(row_ptr + r);
+                        const int64_t k = (int64_t)pr - b;
+                        if (k >= 0 && k < len) atomicOr(&desc[k >> 5], 1u << (k & 31));
+                        if (r < stop && __ldg(row_ptr + r + 1) == pr) dirty = true;
+                        if (r == stop && (int64_t)pr < e) cont = true;
+                    }
                 }
-            }
-        } else {
-            // many (mostly empty) rows: each lane searches the row starts in
-            // its own W positions; dirty follows from the head count below
-            if (lane == 0) {
-                raw0 = (int64_t)pr_chunk == b;
-                cont = stop < a.m && (int64_t)__ldg(row_ptr + stop) < e;
-                if (raw0) atomicOr(&desc[0], 1u);
-            }
-            const int64_t lo = b + (int64_t)lane * W;
-            const int64_t hi = (lo + W < e) ? lo + W : e;
-            for_row_starts<false>(row_ptr, start, stop, lo, hi, [&](int64_t v, int32_t) {
-                const int64_t k = v - b;
-                atomicOr(&desc[k >> 5], 1u << (k & 31));
-            });
-        }
-        dirty = __any_sync(FULL, dirty);
-        cont = __any_sync(FULL, cont);
-        raw0 = __any_sync(FULL, raw0);
-        __syncwarp();
-        const int bit0 = lane * W;
-        const uint64_t win =
-            ((uint64_t)desc[(bit0 >> 5) + 1] << 32) | (uint64_t)desc[bit0 >> 5];
-        uint32_t hb = (uint32_t)(win >> (bit0 & 31)) & ((1u << W) - 1u);
-        if (many_rows) {
-            // rows in [start, stop) minus non-empty ones: the non-empty rows
-            // there are row `start` plus one per row start inside the tile,
-            // except row `stop`'s own start when it continues
-            const int heads = __reduce_add_sync(FULL, (unsigned)__popc(lane == 0 ? hb & ~1u : hb));
-            dirty = (int64_t)(stop - start) > 1 + (int64_t)heads - (cont ? 1 : 0);
-        }
-        if (a.dbg_desc != nullptr && lane < W) a.dbg_desc[t * W + lane] = desc[lane];
-        if (lane == 0) hb |= 1u;  // each tile opens with a segment (Sec. 3.2)
-
-        // ---- compact indices: exclusive scan of head counts (Alg. 1 y_index)
-        const uint32_t hbA = hb & ((1u << HA) - 1u), hbB = hb >> HA;
-        const int cA = __popc(hbA), cB = __popc(hbB);
-        const int c = cA + cB;
-        const int incl = warp_inclusive_scan(c, lane);
-        const int idx0 = incl - c;
-        const int nseg = __shfl_sync(FULL, incl, 31);
-        const A cin = (raw0 || t == t0) ? P::zero() : carry;  // transmitter
-
-        auto emit = [&](int sidx, A v) {
-            if (sidx == 0 && start == rF) {
-                *slot_f = v;
             } else {
-                const int64_t row = (int64_t)start + sidx;
-                if (row < a.m) y[row] = P::out(v);
-                else atomicOr(a.err, SSSPMV_DEV_RANGE);
-            }
-        };
-
-        // ---- per-lane sequential segmented sum, one FMA per entry, as two
-        // interleaved chains; a head closes the open segment (the part before
-        // a chain's first head belongs to a segment opened earlier)
-        A accA = P::zero(), preA = P::zero(), accB = P::zero(), preB = P::zero();
-        int curA = idx0 - 1, curB = idx0 + cA - 1;
-#pragma unroll
-        for (int i = 0; i < HA; ++i) {
-            const int kA = lane * W + i;
-            if ((hbA >> i) & 1u) {
-                if (curA >= idx0) emit(curA, accA);
-                else preA = accA;
-                ++curA;
-                accA = (i == 0 && lane == 0) ? cin : P::zero();
-            }
-            if (kA < len) accA = P::fma(vs[kA], xv[i], accA);
-            if (i < HB) {
-                const int kB = lane * W + HA + i;
-                if ((hbB >> i) & 1u) {
-                    if (curB >= idx0 + cA) emit(curB, accB);
-                    else preB = accB;
-                    ++curB;
-                    accB = P::zero();
+                // many (mostly empty) rows: each lane searches the row starts
+                // in its own W positions; dirty follows from the head count
+                if (lane == 0) {
+                    raw0 = (int64_t)pr_chunk == b;
+                    cont = stop < a.m && (int64_t)__ldg(row_ptr + stop) < e;
+                    if (raw0) atomicOr(&desc[0], 1u);
                 }
-                if (kB < len) accB = P::fma(vs[kB], xv[HA + i], accB);
+                const int64_t lo = b + (int64_t)lane * W;
+                const int64_t hi = (lo + W < e) ? lo + W : e;
+                for_row_starts<false>(row_ptr, start, stop, lo, hi, [&](int64_t v, int32_t) {
+                    const int64_t k = v - b;
+                    atomicOr(&desc[k >> 5], 1u << (k & 31));
+                });
             }
-        }
-        if (cA == 0) preA = accA;  // chain totals when a chain has no head
-        if (cB == 0) preB = accB;
-        // join the chains with one add: A's open part + B's leading part
-        const A join = P::add(accA, preB);
-        if (cA > 0 && cB > 0) emit(idx0 + cA - 1, join);
-        const A pre = (cA > 0) ? preA : join;   // the lane's part before its first head
-        const A v = (cB > 0) ? accB : join;     // suffix if the lane has a head, else total
-        const bool has = c > 0;
+            dirty = __any_sync(FULL, dirty);
+            cont = __any_sync(FULL, cont);
+            raw0 = __any_sync(FULL, raw0);
+            __syncwarp();
+            const int bit0 = lane * W;
+            const uint64_t win =
+                ((uint64_t)desc[(bit0 >> 5) + 1] << 32) | (uint64_t)desc[bit0 >> 5];
+            uint32_t hb = (uint32_t)(win >> (bit0 & 31)) & ((1u << W) - 1u);
+            if (many_rows) {
+                // rows in [start, stop) minus non-empty ones: the non-empty
+                // rows there are row `start` plus one per row start inside
+                // the tile, except row `stop`'s own start when it continues
+                const int heads =
+                    (int)__reduce_add_sync(FULL, (unsigned)__popc(lane == 0 ? hb & ~1u : hb));
+                dirty = (int64_t)(stop - start) > 1 + (int64_t)heads - (cont ? 1 : 0);
+            }
+            if (a.dbg_desc != nullptr && lane < W) a.dbg_desc[t * W + lane] = desc[lane];
+            if (lane == 0) hb |= 1u;  // each tile opens with a segment (Sec. 3.2)
 
-        // ---- cross-lane segmented sum of the open segments:
-        // C_l = sum of v over lanes first_l..l, first_l = last lane <= l with
-        // a head.  Short chains are summed serially, long ones by a scan.
-        const unsigned hm = __ballot_sync(FULL, has);
-        const unsigned le = hm & ((lane == 31) ? FULL : ((2u << lane) - 1u));
-        const int first = 31 - __clz(le);
-        const int span = __reduce_max_sync(FULL, (unsigned)(lane - first));
-        A C = v;
-        if (span <= 4) {
-            for (int d = 1; d <= span; ++d) {
-                const A o = P::shfl_up(v, d);
-                if (lane - d >= first) C = P::add(C, o);
-            }
-        } else {
+            // ---- compact indices: exclusive scan of head counts (y_index)
+            const uint32_t hbA = hb & ((1u << HA) - 1u), hbB = hb >> HA;
+            const int cA = __popc(hbA), cB = __popc(hbB);
+            const int c = cA + cB;
+            const int incl = warp_inclusive_scan(c, lane);
+            const int idx0 = incl - c;
+            const int nseg = __shfl_sync(FULL, incl, 31);
+            const A cin = (raw0 || t == t0) ? P::zero() : carry;  // transmitter
+
+            auto emit = [&](int sidx, A v) {
+                if (sidx == 0 && start == rF) {
+                    *slot_f = v;
+                } else {
+                    const int64_t row = (int64_t)start + sidx;
+                    if (row < a.m) y[row] = P::out(v);
+                    else atomicOr(a.err, SSSPMV_DEV_RANGE);
+                }
+            };
+
+            // ---- per-lane sequential segmented sum, one FMA per entry, as
+            // two interleaved chains; a head closes the open segment (the
+            // part before a chain's first head belongs to an earlier segment)
+            A accA = P::zero(), preA = P::zero(), accB = P::zero(), preB = P::zero();
+            int curA = idx0 - 1, curB = idx0 + cA - 1;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const A o = P::shfl_up(C, d);
-                if (lane - d >= first) C = P::add(C, o);
+            for (int i = 0; i < HA; ++i) {
+                const int kA = lane * W + i;
+                if ((hbA >> i) & 1u) {
+                    if (curA >= idx0) emit(curA, accA);
+                    else preA = accA;
+                    ++curA;
+                    accA = (i == 0 && lane == 0) ? cin : P::zero();
+                }
+                if (kA < len) accA = P::fma(vs[kA], xv[i], accA);
+                if (i < HB) {
+                    const int kB = lane * W + HA + i;
+                    if ((hbB >> i) & 1u) {
+                        if (curB >= idx0 + cA) emit(curB, accB);
+                        else preB = accB;
+                        ++curB;
+                        accB = P::zero();
+                    }
+                    if (kB < len) accB = P::fma(vs[kB], xv[HA + i], accB);
+                }
             }
+            if (cA == 0) preA = accA;  // chain totals when a chain has no head
+            if (cB == 0) preB = accB;
+            // join the chains with one add: A's open part + B's leading part
+            const A join = P::add(accA, preB);
+            if (cA > 0 && cB > 0) emit(idx0 + cA - 1, join);
+            const A pre = (cA > 0) ? preA : join;  // the lane's part before its first head
+            const A v = (cB > 0) ? accB : join;    // suffix if the lane has a head, else total
+            const bool has = c > 0;
+
+            // ---- cross-lane segmented sum of the open segments:
+            // C_l = sum of v over lanes first_l..l, first_l = last lane <= l
+            // with a head.  Short chains are summed serially, long ones by a
+            // scan.
+            const unsigned hm = __ballot_sync(FULL, has);
+            const unsigned le = hm & ((lane == 31) ? FULL : ((2u << lane) - 1u));
+            const int first = 31 - __clz(le);
+            const int span = (int)__reduce_max_sync(FULL, (unsigned)(lane - first));
+            A C = v;
+            if (span <= 4) {
+                for (int d = 1; d <= span; ++d) {
+                    const A o = P::shfl_up(v, d);
+                    if (lane - d >= first) C = P::add(C, o);
+                }
+            } else {
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const A o = P::shfl_up(C, d);
+                    if (lane - d >= first) C = P::add(C, o);
+                }
+            }
+            const A Cprev = P::shfl_up(C, 1);
+            // a lane with a head closes the segment left open before it
+            if (has && lane > 0) emit(idx0 - 1, P::add(Cprev, pre));
+            // the tile's last segment: stored, or carried if row `stop` goes on
+            if (lane == 31) {
+                *slot_carry = C;
+                if (nseg == 1 && start == rF) {
+                    *slot_f = C;  // still the bunch's first segment
+                } else if (cont) {
+                    if (t == t1 - 1) {  // continues into the next bunch
+                        G = C;
+                        hasG = true;
+                    }  // else the next tile of this bunch stores it
+                } else {
+                    emit(nseg - 1, C);
+                }
+            }
+            if (lane == 0) a.tile_info[t] = (uint32_t)nseg | (dirty ? 0x80000000u : 0u);
+            __syncwarp();
+            carry = *slot_carry;
+            ++q_con;
+            issue_next();  // the stage just consumed takes the next copy
+            start = start_nx;
+            stop = stop_nx;
+            pr_chunk = pr_nx;
         }
-        const A Cprev = P::shfl_up(C, 1);
-        // a lane with a head closes the segment left open before it
-        if (has && lane > 0) emit(idx0 - 1, P::add(Cprev, pre));
-        // the tile's last segment: stored, or carried if row `stop` goes on
+        // ---- synchronizer record of the bunch; its sums are finished in FP64
+        __syncwarp();
+        const A F = *slot_f;
         if (lane == 31) {
-            *slot_carry = C;
-            if (nseg == 1 && start == rF) {
-                *slot_f = C;          // still the bunch's first segment
-            } else if (cont) {
-                if (t == t1 - 1) {    // continues into the next bunch
-                    G = C;
-                    hasG = true;
-                }                     // else the next tile of this bunch stores it
-            } else {
-                emit(nseg - 1, C);
-            }
+            a.sync_idx[cur] = rF;
+            static_cast<double *>(a.sync_val)[cur] = P::to_f64(F);
+            static_cast<double *>(a.tail_val)[cur] = hasG ? P::to_f64(G) : 0.0;
+            a.tail_flag[cur] = hasG ? 1 : 0;
         }
-        if (lane == 0) a.tile_info[t] = (uint32_t)nseg | (dirty ? 0x80000000u : 0u);
-        __syncwarp();
-        carry = *slot_carry;
-        // ---- release the stage: copy the tile STAGES ahead into it
-        if (lane == 0 && t + STAGES < t1) {
-            fence_proxy_async_smem();
-            issue(t + STAGES, s);
-        }
-        start = stop;
-        stop = stop_nx;
-        pr_chunk = pr_nx;
-    }
-    __syncwarp();
-    F = *slot_f;
-    if (lane == 31) {
-        // synchronizer record of this bunch; its sums are finished in FP64
-        a.sync_idx[w] = rF;
-        static_cast<double *>(a.sync_val)[w] = P::to_f64(F);
-        static_cast<double *>(a.tail_val)[w] = hasG ? P::to_f64(G) : 0.0;
-        a.tail_flag[w] = hasG ? 1 : 0;
+        claim_next();
+        cur = nxt;
+        nxt = -1;
+        if (cur >= a.nbunches) break;
     }
 }
 
@@ -648,28 +695,68 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
     }
     blk -= a.nblk_tiles;
     if (blk < a.nblk_sync) {
-        // ---- synchronization (Alg. 1 synchronization step, on the GPU): the
-        // run of bunches sharing a first row adds into that row, plus the
-        // tail partial the previous bunch left for it
-        const int64_t w = (int64_t)blk * kCalibWarps + warp;
-        if (w >= a.nbunches) return;
-        const int32_t r = __ldg(a.sync_idx + w);
-        if (w > 0 && __ldg(a.sync_idx + w - 1) == r) return;
+        // ---- synchronization (Alg. 1's synchronization step, on the GPU):
+        // the run of bunches sharing a first row adds into that row, plus the
+        // tail partial the bunch before the run left for it.  A warp covers
+        // 32 bunches, one per lane; runs are summed by a segmented warp scan
+        // and a run that goes on past the window is finished by this warp.
         const double *sv = static_cast<const double *>(a.sync_val);
-        double acc = 0.0;  // calibration sums are kept in FP64
-        for (int64_t base = w;; base += 32) {
-            const int64_t ww = base + lane;
-            const bool in = ww < a.nbunches && __ldg(a.sync_idx + ww) == r;
-            if (in) acc += sv[ww];
-            if (__popc(__ballot_sync(FULL, in)) < 32) break;
-        }
+        const double *tv = static_cast<const double *>(a.tail_val);
+        const int64_t base = ((int64_t)blk * kCalibWarps + warp) * 32;
+        const int64_t w = base + lane;
+        const bool valid = w < a.nbunches;
+        const int32_t r = valid ? __ldg(a.sync_idx + w) : -1;
+        int32_t rprev = __shfl_up_sync(FULL, r, 1);
+        if (lane == 0) rprev = (valid && w > 0) ? __ldg(a.sync_idx + w - 1) : -1;
+        const bool lead = valid && (w == 0 || rprev != r);
+        const unsigned lmask = __ballot_sync(FULL, lead);
+        if (lmask == 0) return;  // the whole window continues a run led earlier
+        const int firstlead = __ffs(lmask) - 1;
+        const bool owned = valid && lane >= firstlead;
+        // segmented inclusive sum over runs (heads: leaders and invalid lanes)
+        const bool head = lead || !valid;
+        const unsigned hmask = __ballot_sync(FULL, head) | 1u;
+        const unsigned le = hmask & ((lane == 31) ? FULL : ((2u << lane) - 1u));
+        const int first = 31 - __clz(le);
+        double C = valid ? sv[w] : 0.0;
 #pragma unroll
-        for (int d = 16; d >= 1; d >>= 1) acc += __shfl_xor_sync(FULL, acc, d);
-        if (lane == 0) {
-            if (w > 0 && __ldg(a.tail_flag + w - 1))
-                acc += static_cast<const double *>(a.tail_val)[w - 1];
-            if (r >= 0 && r < a.m) y[r] = (Y)acc;
+        for (int d = 1; d < 32; d <<= 1) {
+            const double o = __shfl_up_sync(FULL, C, d);
+            if (lane - d >= first) C += o;
+        }
+        // does this lane's run go on to the next bunch?
+        bool next_same;
+        const bool next_lead = __shfl_down_sync(FULL, lead, 1);
+        const bool next_valid = __shfl_down_sync(FULL, valid, 1);
+        if (lane < 31) next_same = next_valid && !next_lead;
+        else next_same = valid && w + 1 < a.nbunches && __ldg(a.sync_idx + w + 1) == r;
+        if (owned && !next_same) {
+            const int64_t wl = base + first;  // the run's leader
+            double total = C;
+            if (wl > 0 && __ldg(a.tail_flag + wl - 1)) total += tv[wl - 1];
+            if (r >= 0 && r < a.m) y[r] = (Y)total;
             else atomicOr(a.err, SSSPMV_DEV_RANGE);
+        }
+        const bool open = __shfl_sync(FULL, owned && next_same, 31);
+        if (open) {  // the last run continues past the window (long rows)
+            const int32_t rr = __shfl_sync(FULL, r, 31);
+            const double csum = __shfl_sync(FULL, C, 31);
+            const int64_t wl = base + __shfl_sync(FULL, first, 31);
+            double acc = 0.0;
+            for (int64_t b2 = base + 32;; b2 += 32) {
+                const int64_t ww = b2 + lane;
+                const bool in = ww < a.nbunches && __ldg(a.sync_idx + ww) == rr;
+                if (in) acc += sv[ww];
+                if (__popc(__ballot_sync(FULL, in)) < 32) break;
+            }
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1) acc += __shfl_xor_sync(FULL, acc, d);
+            if (lane == 0) {
+                double total = csum + acc;
+                if (wl > 0 && __ldg(a.tail_flag + wl - 1)) total += tv[wl - 1];
+                if (rr >= 0 && rr < a.m) y[rr] = (Y)total;
+                else atomicOr(a.err, SSSPMV_DEV_RANGE);
+            }
         }
         return;
     }
