@@ -64,14 +64,29 @@ extern "C" {
 #define SSSPMV_DEV_RANGE     2u  /* a computed row index fell outside [0, m) */
 #define SSSPMV_DEV_CALIB     4u  /* calibration found a segment count that does not match row_ptr */
 
+/* Storing the partial sums of tiles that hold empty rows ("dirty" tiles):
+ *  SPECULATIVE  the paper's method: kernel (b) stores every segment at its
+ *               speculative row tile_offset[t] + s and kernel (c) moves the
+ *               partials of dirty tiles to their rows and zeroes empty rows
+ *               (Sec. 3.2, checking prediction).  The default.
+ *  EXACT        kernel (b) resolves dirty tiles on chip: it already reads the
+ *               tile's row pointers, so it stores each partial at the row that
+ *               starts at the segment's head and zeroes the empty rows itself;
+ *               kernel (c) only finishes the synchronizer sums.  Same y. */
+#define SSSPMV_VARIANT_DEFAULT     0
+#define SSSPMV_VARIANT_SPECULATIVE 1
+#define SSSPMV_VARIANT_EXACT       2
+
 /* Tile and launch parameters (Sec. 3.1, Table 3).  Zero-initialise and set
  * only what you need; a NULL opts pointer means all defaults. */
 typedef struct ssspmv_opts {
     int32_t W;         /* entries per lane (odd, see ssspmv_supported_w); L = 32*W.
                           0 = pick from the mean row length nnz/m */
-    int32_t S;         /* tiles per thread-bunch (warp); 0 = one wave of warps */
+    int32_t S;         /* tiles per thread-bunch (warp); 0 = 4.  Bunches are handed
+                          to a persistent grid of warps in order, each warp taking
+                          the next unclaimed bunch */
     int32_t validate;  /* reserved, must be 0 (use ssspmv_validate_csr) */
-    int32_t reserved;
+    int32_t variant;   /* SSSPMV_VARIANT_*: how tiles holding empty rows are stored */
     void   *timer;     /* optional ssspmv_timer*: the call records its kernel
                           boundaries into the timer's next slot; NULL = none */
 } ssspmv_opts;
@@ -169,7 +184,8 @@ int ssspmv_csr_f64_host(int32_t m, int32_t n, int32_t nnz,
  *                           of tile t is bit k%32 of word t*W + k/32, set iff a
  *                           row starts at entry t*L + k (bit 0 NOT forced)
  *   tile_info[ntiles]       bit 31 = dirty (an empty row in [start, stop)),
- *                           bits 0..30 = number of segments of the tile
+ *                           bit 30 = dirty and resolved in kernel (b) (EXACT),
+ *                           bits 0..29 = number of segments of the tile
  *   sync_idx[nbunches]      synchronizer row of each bunch (= tile_offset[w*S])
  *   y_spec[m]               y after kernel (b), before calibration (entries
  *                           kernel (b) does not write are left as y held them)

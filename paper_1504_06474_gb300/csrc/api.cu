@@ -99,7 +99,8 @@ static int resolve_w(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_opt
 static int make_layout(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_opts *o, Layout &l)
 {
     if (m < 0 || nnz < 0) return SSSPMV_EINVAL;
-    if (o && (o->S < 0 || o->validate != 0)) return SSSPMV_EINVAL;
+    if (o && (o->S < 0 || o->validate != 0 || o->variant < 0 || o->variant > 2))
+        return SSSPMV_EINVAL;
     int32_t W = 0;
     int rc = resolve_w(m, nnz, val_bytes, o, &W);
     if (rc) return rc;
@@ -177,6 +178,7 @@ static int run_call(int32_t val_bytes, int32_t m, int32_t n, int32_t nnz,
                                  : nullptr;
     c.dbg_desc = dbg_desc;
     c.dbg_yspec = dbg_yspec;
+    c.exact = (opts && opts->variant == SSSPMV_VARIANT_EXACT) ? 1 : 0;
     return pr->run(c);
 }
 

@@ -18,6 +18,7 @@ struct Call {
     unsigned char *ws = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t *ev = nullptr;       // 4 library-owned events or null
+    int exact = 0;                   // dirty tiles store in their true rows
     uint32_t *dbg_desc = nullptr;    // ntiles*W words or null
     void *dbg_yspec = nullptr;       // m values or null
 };
@@ -32,12 +33,13 @@ template <class P, int W>
 int segsum_resident_warps()
 {
     using SM = WarpSmem<P, W>;
-    constexpr int B = pick_bunches_per_block(SM::BYTES);
+    constexpr BlockShape BS = pick_block_shape(SM::BYTES, P::kMaxWarps);
+    constexpr int B = BS.B;
     static int cache[64] = {0};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
     if (cache[dev] > 0) return cache[dev];
-    auto kb = segsum_kernel<P, W, B>;
+    auto kb = segsum_kernel<P, W, B, BS.blocks>;
     int nb = 0;
     if (cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, B * SM::BYTES) !=
             cudaSuccess ||
@@ -63,7 +65,8 @@ template <class P, int W>
 int run_shape(const Call &c)
 {
     using SM = WarpSmem<P, W>;
-    constexpr int B = pick_bunches_per_block(SM::BYTES);
+    constexpr BlockShape BS = pick_block_shape(SM::BYTES, P::kMaxWarps);
+    constexpr int B = BS.B;
     const Layout &l = c.lay;
     unsigned char *ws = c.ws;
     uint32_t *err = reinterpret_cast<uint32_t *>(ws + l.off_err);
@@ -104,7 +107,8 @@ int run_shape(const Call &c)
         a.ntiles = l.ntiles;
         a.nbunches = l.nbunches;
         a.S = l.S;
-        auto kb = segsum_kernel<P, W, B>;
+        a.exact = c.exact;
+        auto kb = segsum_kernel<P, W, B, BS.blocks>;
         static int attr_done[64] = {0};
         int dev = 0;
         cudaGetDevice(&dev);

@@ -5,6 +5,9 @@
 
 #include "ssspmv.h"
 
+// odd W values (entries per lane) compiled for every precision
+#define SSSPMV_SHAPES(X) X(15) X(21) X(27) X(31)
+
 namespace ssspmv {
 
 // tiles per thread-bunch when the caller does not choose S: small bunches,

@@ -41,11 +41,12 @@ __global__ void __launch_bounds__(kPartitionThreads)
 // row_ptr[r+1]), which is the rightmost row with row_ptr[r] <= b_t; so each
 // non-empty row writes its index to the boundaries it contains.  Reads
 // row_ptr once, coalesced, instead of ~log2(m) dependent probes per boundary.
+template <int W>
 __global__ void __launch_bounds__(kPartitionThreads)
     partition_scatter_kernel(const int32_t *__restrict__ row_ptr, int32_t m, int32_t nnz,
-                             int32_t L, int64_t ntiles, int32_t *__restrict__ tile_offset,
-                             uint32_t *err)
+                             int64_t ntiles, int32_t *__restrict__ tile_offset, uint32_t *err)
 {
+    constexpr int64_t L = 32 * W;  // a compile-time divisor
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i0 == 0) {
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(kPartitionThreads)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             // tiles t with lo <= t*L < hi
-            for (int64_t t = (lo[u] + (int64_t)L - 1) / L; t * L < hi[u]; ++t)
+            for (int64_t t = ((uint32_t)lo[u] + (uint32_t)(L - 1)) / (uint32_t)L; t * L < hi[u]; ++t)
                 tile_offset[t] = (int32_t)(r0 + u * stride);
         }
     }
@@ -81,13 +82,20 @@ void launch_partition(const int32_t *row_ptr, int32_t m, int32_t nnz, int32_t L,
                       int32_t *tile_offset, uint32_t *err, cudaStream_t stream, int method)
 {
     if (method == 1) {
-        int64_t blocks = ((int64_t)m + kPartitionThreads - 1) / kPartitionThreads;
+        int64_t blocks = ((int64_t)m + 4 * kPartitionThreads - 1) / (4 * kPartitionThreads);
         const int64_t cap = 8LL * device_sm_count();
         if (blocks > cap) blocks = cap;
         if (blocks < 1) blocks = 1;
-        partition_scatter_kernel<<<(unsigned)blocks, kPartitionThreads, 0, stream>>>(
-            row_ptr, m, nnz, L, ntiles, tile_offset, err);
+        switch (L / 32) {
+#define X(w)                                                                                   \
+    case w:                                                                                    \
+        partition_scatter_kernel<w><<<(unsigned)blocks, kPartitionThreads, 0, stream>>>(       \
+            row_ptr, m, nnz, ntiles, tile_offset, err);                                        \
         return;
+            SSSPMV_SHAPES(X)
+#undef X
+        default: break;  // other tile lengths use the search
+        }
     }
     const int64_t nthreads = ntiles + 1;
     const unsigned grid = (unsigned)((nthreads + kPartitionThreads - 1) / kPartitionThreads);

@@ -29,6 +29,7 @@ namespace ssspmv {
 // precision traits
 
 struct F64 {
+    static constexpr int kMaxWarps = 16;  // 128 registers per thread
     using val_t = double;
     using x_t = double;
     using y_t = double;
@@ -76,6 +77,7 @@ __device__ __forceinline__ CompF32 comp_fma(float v, float x, CompF32 a)
 
 template <class V>
 struct CompF32Traits {
+    static constexpr int kMaxWarps = 20;  // 96 registers per thread
     using val_t = V;
     using x_t = float;
     using y_t = float;
@@ -115,65 +117,6 @@ void launch_partition(const int32_t *row_ptr, int32_t m, int32_t nnz, int32_t L,
 int partition_method(int32_t m, int64_t ntiles);
 
 // ---------------------------------------------------------------------------
-// row-pointer searches used when a tile spans many (mostly empty) rows
-
-// first j in [lo, hi] with row_ptr[j] >= p, or hi + 1 if none
-__device__ __forceinline__ int32_t rp_lower_bound(const int32_t *__restrict__ row_ptr,
-                                                  int32_t lo, int32_t hi, int64_t p)
-{
-    int32_t a = lo, z = hi + 1;
-    while (a < z) {
-        const int32_t mid = a + ((z - a) >> 1);
-        if ((int64_t)__ldg(row_ptr + mid) < p) a = mid + 1;
-        else z = mid;
-    }
-    return a;
-}
-
-// last j in [lo, hi] with row_ptr[j] <= p (row_ptr[lo] <= p assumed)
-__device__ __forceinline__ int32_t rp_rightmost(const int32_t *__restrict__ row_ptr, int32_t lo,
-                                               int32_t hi, int64_t p)
-{
-    int32_t a = lo, z = hi;
-    while (a < z) {
-        const int32_t mid = a + ((z - a + 1) >> 1);
-        if ((int64_t)__ldg(row_ptr + mid) <= p) a = mid;
-        else z = mid - 1;
-    }
-    return a;
-}
-
-// Row starts inside tile positions [lo, hi) (absolute entry indices): calls
-// f(pos, r) for each distinct start position pos and the non-empty row r that
-// begins there (when need_row; r = -1 otherwise), among rows (start, stop].
-// O(heads * log(stop - start)) probes instead of a walk over every row.
-template <bool need_row, class F>
-__device__ __forceinline__ void for_row_starts(const int32_t *__restrict__ row_ptr, int32_t start,
-                                               int32_t stop, int64_t lo, int64_t hi, F &&f)
-{
-    int64_t p = lo;
-    int32_t jlo = start + 1;
-    while (p < hi && jlo <= stop) {
-        const int32_t j = rp_lower_bound(row_ptr, jlo, stop, p);
-        if (j > stop) break;
-        const int64_t v = __ldg(row_ptr + j);
-        if (v >= hi) break;
-        int32_t r = -1;
-        if (need_row) {
-            r = rp_rightmost(row_ptr, j, stop, v);
-            jlo = r + 1;
-        } else {
-            jlo = j + 1;
-        }
-        f(v, r);
-        p = v + 1;
-    }
-}
-
-// tiles spanning more rows than this use the searches above
-constexpr int32_t kScanRows = 63;
-
-// ---------------------------------------------------------------------------
 // shared-memory layout of one warp in kernel (b)
 
 template <class P, int W>
@@ -191,21 +134,30 @@ struct WarpSmem {
     static constexpr int BYTES = (SLOT_OFF + 32 + 127) & ~127;
 };
 
-// warps per block maximising resident warps per SM for a given per-warp
-// shared-memory footprint (228 KB per SM, 227 KB per block, 1 KB reserved
-// per block)
-constexpr int pick_bunches_per_block(int warp_bytes)
+// Warps per block (B) and blocks per SM maximising resident warps per SM for
+// a per-warp shared-memory footprint (228 KB per SM, 227 KB per block, 1 KB
+// reserved per block) under a register budget of max_warps warps per SM.
+struct BlockShape {
+    int B, blocks;
+};
+
+constexpr BlockShape pick_block_shape(int warp_bytes, int max_warps)
 {
-    int best_b = 1, best_w = 0;
-    for (int b = 1; b <= 32; ++b) {
-        long blk = (long)b * warp_bytes;
+    BlockShape best{1, 1};
+    int best_w = 0;
+    for (int b = 1; b <= 32 && b <= max_warps; ++b) {
+        const long blk = (long)b * warp_bytes;
         if (blk > 232448) break;
         int per_sm = (int)(233472 / (blk + 1024));
-        if (per_sm > 32 / b + 1) per_sm = 32 / b + 1;
-        int w = per_sm * b;
-        if (w >= best_w) { best_w = w; best_b = b; }
+        if (per_sm * b > max_warps) per_sm = max_warps / b;
+        if (per_sm < 1) continue;
+        const int w = per_sm * b;
+        if (w >= best_w) {
+            best_w = w;
+            best = BlockShape{b, per_sm};
+        }
     }
-    return best_b;
+    return best;
 }
 
 struct SegsumArgs {
@@ -228,7 +180,14 @@ struct SegsumArgs {
     int64_t ntiles;
     int64_t nbunches;
     int32_t S;
+    int32_t exact;       // 1: dirty tiles store their partials in their true rows
 };
+
+// tile_info layout: bit 31 dirty, bit 30 dirty and resolved by kernel (b),
+// bits 0..29 number of segments
+constexpr uint32_t kInfoDirty = 0x80000000u;
+constexpr uint32_t kInfoResolved = 0x40000000u;
+constexpr uint32_t kInfoSegMask = 0x3fffffffu;
 
 // ---------------------------------------------------------------------------
 // kernel (b): a thread-bunch (warp) processes S consecutive tiles, carrying the
@@ -238,8 +197,8 @@ struct SegsumArgs {
 // cores, without refilling the copy pipeline at every bunch (the copies of a
 // warp's next bunch are issued while it finishes the current one).
 
-template <class P, int W, int B>
-__global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
+template <class P, int W, int B, int MINB>
+__global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a)
 {
     using V = typename P::val_t;
     using X = typename P::x_t;
@@ -327,6 +286,7 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
     int32_t start = __ldg(a.tile_offset + cur * S);
     int32_t stop = __ldg(a.tile_offset + cur * S + 1);
     int32_t pr_chunk = __ldg(row_ptr + (start + lane < a.m ? start + lane : a.m));
+    int32_t pr_chunk2 = __ldg(row_ptr + (start + 32 + lane < a.m ? start + 32 + lane : a.m));
 
     constexpr int HA = (W + 1) / 2;  // each lane's run is two FMA chains:
     constexpr int HB = W - HA;       // entries [0, HA) and [HA, W)
@@ -347,7 +307,7 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
 
             // ---- prefetch the next tile's rows (the next bunch's first tile
             // after the last one)
-            int32_t start_nx = stop, stop_nx = 0, pr_nx = 0;
+            int32_t start_nx = stop, stop_nx = 0, pr_nx = 0, pr_nx2 = 0;
             bool have_nx = true;
             if (t + 1 < t1) {
                 stop_nx = __ldg(a.tile_offset + t + 2);
@@ -360,7 +320,10 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
                     have_nx = false;
                 }
             }
-            if (have_nx) pr_nx = __ldg(row_ptr + (start_nx + lane < a.m ? start_nx + lane : a.m));
+            if (have_nx) {
+                pr_nx = __ldg(row_ptr + (start_nx + lane < a.m ? start_nx + lane : a.m));
+                pr_nx2 = __ldg(row_ptr + (start_nx + 32 + lane < a.m ? start_nx + 32 + lane : a.m));
+            }
 
             // ---- wait for this tile's val/col
             unsigned char *st = stage_ptr(s);
@@ -396,66 +359,69 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
             // ---- segment descriptor built on chip from row_ptr[start..stop]
             // (Sec. 3.2: offsets of the covered row pointers from the
             // boundary; every row start inside the tile, including row
-            // `stop`'s) and the empty-row ("dirty") test over [start, stop)
+            // `stop`'s) and the empty-row ("dirty") test over [start, stop).
+            // With exact stores, a map from tile position to the non-empty
+            // row starting there goes into the stage's column region (free
+            // once the gathers above are issued) and empty rows are zeroed.
+            const bool exact = a.exact != 0;
+            int32_t *rowmap = reinterpret_cast<int32_t *>(st + SM::VAL_REGION);
             if (lane <= W) desc[lane] = 0u;
             __syncwarp();
             bool dirty = false, cont = false, raw0 = false;
-            const bool many_rows = stop - start > kScanRows;
-            if (!many_rows) {
-                {
-                    const int32_t r = start + lane;
-                    const int32_t pr = pr_chunk;
-                    int32_t nx = __shfl_down_sync(FULL, pr, 1);
-                    if (lane == 31 && r < stop) nx = __ldg(row_ptr + r + 1);
-                    if (r <= stop) {
-                        const int64_t k = (int64_t)pr - b;
-                        if (k >= 0 && k < len) atomicOr(&desc[k >> 5], 1u << (k & 31));
-                        if (r < stop && nx == pr) dirty = true;
-                        if (lane == 0 && k == 0) raw0 = true;
-                        if (r == stop && (int64_t)pr < e) cont = true;
+            auto scan_row = [&](int64_t r, int32_t pr, int32_t nx) {
+                if (r > stop) return;
+                const int64_t k = (int64_t)pr - b;
+                if (k >= 0 && k < len) atomicOr(&desc[k >> 5], 1u << (k & 31));
+                if (r < stop) {
+                    if (nx == pr) {
+                        dirty = true;
+                        if (exact) y[r] = Y(0);  // r > start: row `start` is never empty
+                    } else if (exact && k > 0) {
+                        rowmap[k] = (int32_t)r;
                     }
                 }
-                if (start + 32 <= stop) {  // second chunk
-                    const int32_t r = start + 32 + lane;
-                    if (r <= stop) {
-                        const int32_t pr = __ldg(row_ptr + r);
-                        const int64_t k = (int64_t)pr - b;
-                        if (k >= 0 && k < len) atomicOr(&desc[k >> 5], 1u << (k & 31));
-                        if (r < stop && __ldg(row_ptr + r + 1) == pr) dirty = true;
-                        if (r == stop && (int64_t)pr < e) cont = true;
+                if (r == start && k == 0) raw0 = true;
+                if (r == stop && (int64_t)pr < e) cont = true;
+            };
+            {
+                // the first two chunks of 32 rows were loaded one tile ahead
+                const int32_t head2 = __shfl_sync(FULL, pr_chunk2, 0);
+                int32_t nx = __shfl_down_sync(FULL, pr_chunk, 1);
+                if (lane == 31) nx = head2;
+                scan_row((int64_t)start + lane, pr_chunk, nx);
+                if ((int64_t)start + 32 <= stop) {
+                    nx = __shfl_down_sync(FULL, pr_chunk2, 1);
+                    if (lane == 31 && (int64_t)start + 63 < stop) nx = __ldg(row_ptr + start + 64);
+                    scan_row((int64_t)start + 32 + lane, pr_chunk2, nx);
+                }
+                // longer row ranges: four chunks per round trip
+                for (int64_t rb = (int64_t)start + 64; rb <= stop; rb += 128) {
+                    int32_t prs[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int64_t r = rb + 32 * u + lane;
+                        prs[u] = __ldg(row_ptr + (r < a.m ? r : a.m));
+                    }
+                    int32_t tail = 0;
+                    if (lane == 31 && rb + 127 < stop) tail = __ldg(row_ptr + rb + 128);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int32_t nlead = __shfl_sync(FULL, prs[u < 3 ? u + 1 : 3], 0);
+                        int32_t n2 = __shfl_down_sync(FULL, prs[u], 1);
+                        if (lane == 31) n2 = (u < 3) ? nlead : tail;
+                        scan_row(rb + 32 * u + lane, prs[u], n2);
                     }
                 }
-            } else {
-                // many (mostly empty) rows: each lane searches the row starts
-                // in its own W positions; dirty follows from the head count
-                if (lane == 0) {
-                    raw0 = (int64_t)pr_chunk == b;
-                    cont = stop < a.m && (int64_t)__ldg(row_ptr + stop) < e;
-                    if (raw0) atomicOr(&desc[0], 1u);
-                }
-                const int64_t lo = b + (int64_t)lane * W;
-                const int64_t hi = (lo + W < e) ? lo + W : e;
-                for_row_starts<false>(row_ptr, start, stop, lo, hi, [&](int64_t v, int32_t) {
-                    const int64_t k = v - b;
-                    atomicOr(&desc[k >> 5], 1u << (k & 31));
-                });
             }
             dirty = __any_sync(FULL, dirty);
             cont = __any_sync(FULL, cont);
             raw0 = __any_sync(FULL, raw0);
             __syncwarp();
+            const bool resolve = exact && dirty;
             const int bit0 = lane * W;
             const uint64_t win =
                 ((uint64_t)desc[(bit0 >> 5) + 1] << 32) | (uint64_t)desc[bit0 >> 5];
             uint32_t hb = (uint32_t)(win >> (bit0 & 31)) & ((1u << W) - 1u);
-            if (many_rows) {
-                // rows in [start, stop) minus non-empty ones: the non-empty
-                // rows there are row `start` plus one per row start inside
-                // the tile, except row `stop`'s own start when it continues
-                const int heads =
-                    (int)__reduce_add_sync(FULL, (unsigned)__popc(lane == 0 ? hb & ~1u : hb));
-                dirty = (int64_t)(stop - start) > 1 + (int64_t)heads - (cont ? 1 : 0);
-            }
             if (a.dbg_desc != nullptr && lane < W) a.dbg_desc[t * W + lane] = desc[lane];
             if (lane == 0) hb |= 1u;  // each tile opens with a segment (Sec. 3.2)
 
@@ -468,11 +434,16 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
             const int nseg = __shfl_sync(FULL, incl, 31);
             const A cin = (raw0 || t == t0) ? P::zero() : carry;  // transmitter
 
-            auto emit = [&](int sidx, A v) {
+            // segment sidx, whose head is at tile position hpos, goes to the
+            // synchronizer slot (the bunch's first segment), to its
+            // speculative row start + sidx (Alg. 1), or -- exact stores on a
+            // dirty tile -- to the row that starts at hpos
+            auto emit = [&](int sidx, A v, int hpos) {
                 if (sidx == 0 && start == rF) {
                     *slot_f = v;
                 } else {
-                    const int64_t row = (int64_t)start + sidx;
+                    const int64_t row = resolve ? (hpos <= 0 ? (int64_t)start : (int64_t)rowmap[hpos])
+                                                : (int64_t)start + sidx;
                     if (row < a.m) y[row] = P::out(v);
                     else atomicOr(a.err, SSSPMV_DEV_RANGE);
                 }
@@ -483,22 +454,25 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
             // part before a chain's first head belongs to an earlier segment)
             A accA = P::zero(), preA = P::zero(), accB = P::zero(), preB = P::zero();
             int curA = idx0 - 1, curB = idx0 + cA - 1;
+            int posA = -1, posB = -1;  // tile position of each chain's last head
 #pragma unroll
             for (int i = 0; i < HA; ++i) {
                 const int kA = lane * W + i;
                 if ((hbA >> i) & 1u) {
-                    if (curA >= idx0) emit(curA, accA);
+                    if (curA >= idx0) emit(curA, accA, posA);
                     else preA = accA;
                     ++curA;
+                    posA = kA;
                     accA = (i == 0 && lane == 0) ? cin : P::zero();
                 }
                 if (kA < len) accA = P::fma(vs[kA], xv[i], accA);
                 if (i < HB) {
                     const int kB = lane * W + HA + i;
                     if ((hbB >> i) & 1u) {
-                        if (curB >= idx0 + cA) emit(curB, accB);
+                        if (curB >= idx0 + cA) emit(curB, accB, posB);
                         else preB = accB;
                         ++curB;
+                        posB = kB;
                         accB = P::zero();
                     }
                     if (kB < len) accB = P::fma(vs[kB], xv[HA + i], accB);
@@ -508,7 +482,8 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
             if (cB == 0) preB = accB;
             // join the chains with one add: A's open part + B's leading part
             const A join = P::add(accA, preB);
-            if (cA > 0 && cB > 0) emit(idx0 + cA - 1, join);
+            if (cA > 0 && cB > 0) emit(idx0 + cA - 1, join, posA);
+            const int lastpos = (cB > 0) ? posB : posA;  // the lane's last head
             const A pre = (cA > 0) ? preA : join;  // the lane's part before its first head
             const A v = (cB > 0) ? accB : join;    // suffix if the lane has a head, else total
             const bool has = c > 0;
@@ -535,8 +510,14 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
                 }
             }
             const A Cprev = P::shfl_up(C, 1);
+            // head positions of the segments left open: the last head of the
+            // nearest earlier lane with one, and of lane `first` for lane 31
+            const unsigned below = hm & ((1u << lane) - 1u);
+            const int src = below ? 31 - __clz(below) : 0;
+            const int prevpos = __shfl_sync(FULL, lastpos, src);
+            const int openpos = __shfl_sync(FULL, lastpos, first);
             // a lane with a head closes the segment left open before it
-            if (has && lane > 0) emit(idx0 - 1, P::add(Cprev, pre));
+            if (has && lane > 0) emit(idx0 - 1, P::add(Cprev, pre), prevpos);
             // the tile's last segment: stored, or carried if row `stop` goes on
             if (lane == 31) {
                 *slot_carry = C;
@@ -548,10 +529,12 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
                         hasG = true;
                     }  // else the next tile of this bunch stores it
                 } else {
-                    emit(nseg - 1, C);
+                    emit(nseg - 1, C, openpos);
                 }
             }
-            if (lane == 0) a.tile_info[t] = (uint32_t)nseg | (dirty ? 0x80000000u : 0u);
+            if (lane == 0)
+                a.tile_info[t] = (uint32_t)nseg | (dirty ? kInfoDirty : 0u) |
+                                 (resolve ? kInfoResolved : 0u);
             __syncwarp();
             carry = *slot_carry;
             ++q_con;
@@ -559,6 +542,7 @@ __global__ void __launch_bounds__(B * 32, 1) segsum_kernel(const SegsumArgs a)
             start = start_nx;
             stop = stop_nx;
             pr_chunk = pr_nx;
+            pr_chunk2 = pr_nx2;
         }
         // ---- synchronizer record of the bunch; its sums are finished in FP64
         __syncwarp();
@@ -604,73 +588,44 @@ struct CalibArgs {
 
 constexpr int kCalibWarps = 8;
 
-// re-arrangement of one dirty tile by a warp: the s-th partial (s >= 1,
-// speculatively at y[start+s]) moves to the s-th non-empty row inside
-// (start, stop); the other rows there become 0.
+// re-arrangement of one dirty tile by a warp (Sec. 3.2, checking
+// prediction): the s-th partial (s >= 1, speculatively at y[start+s]) moves to
+// the s-th non-empty row inside (start, stop), and the empty rows there become
+// 0.  Rows are walked downwards so that every slot is read before any write
+// can reach it (a partial only moves up).
 template <class P>
 __device__ __forceinline__ void repair_dirty_tile(const CalibArgs &a, int64_t t, uint32_t info,
                                                   int lane)
 {
     using Y = typename P::y_t;
-    constexpr int kMaxHeadsPerLane = 32;
     Y *__restrict__ y = static_cast<Y *>(a.y);
     const int32_t *__restrict__ row_ptr = a.row_ptr;
-    const int32_t nseg = (int32_t)(info & 0x7fffffffu);
+    const int32_t nseg = (int32_t)(info & kInfoSegMask);
     const int32_t start = __ldg(a.tile_offset + t);
     const int32_t stop = __ldg(a.tile_offset + t + 1);
-    const int64_t b = t * (int64_t)a.L;
-    const int64_t e = b + a.L < a.nnz ? b + a.L : a.nnz;
+    const int64_t e = (t + 1) * (int64_t)a.L < a.nnz ? (t + 1) * (int64_t)a.L : a.nnz;
     const bool cont = stop < a.m && (int64_t)__ldg(row_ptr + stop) < e;
     // non-empty rows strictly inside (start, stop): each holds one segment
     const int32_t K = nseg - 1 - (cont ? 1 : 0);
-    if (stop - start <= kScanRows + 1 || a.L > 32 * kMaxHeadsPerLane) {
-        // short range: walk down from stop-1 so that every slot is read before
-        // any write can reach it (the s-th partial moves from start+s up)
-        int32_t above = 0;
-        for (int32_t hi = stop - 1; hi > start; hi -= 32) {
-            const int32_t r = hi - lane;
-            const bool valid = r > start;
-            const bool ne = valid && __ldg(row_ptr + r + 1) > __ldg(row_ptr + r);
-            const unsigned mask = __ballot_sync(FULL, ne);
-            const int32_t q = above + __popc(mask & ((1u << lane) - 1u));
-            Y v = Y(0);
-            if (ne) {
-                const int32_t sidx = K - q;
-                if (sidx >= 1 && sidx <= K) v = y[start + sidx];
-                else atomicOr(a.err, SSSPMV_DEV_CALIB);
-            }
-            __syncwarp();
-            if (valid) y[r] = ne ? v : Y(0);
-            above += __popc(mask);
-            __syncwarp();
+    int32_t above = 0;
+    for (int32_t hi = stop - 1; hi > start; hi -= 32) {
+        const int32_t r = hi - lane;
+        const bool valid = r > start;
+        const bool ne = valid && __ldg(row_ptr + r + 1) > __ldg(row_ptr + r);
+        const unsigned mask = __ballot_sync(FULL, ne);
+        const int32_t q = above + __popc(mask & ((1u << lane) - 1u));
+        Y v = Y(0);
+        if (ne) {
+            const int32_t sidx = K - q;
+            if (sidx >= 1 && sidx <= K) v = y[start + sidx];
+            else atomicOr(a.err, SSSPMV_DEV_CALIB);
         }
-        if (lane == 0 && above != K) atomicOr(a.err, SSSPMV_DEV_CALIB);
-        return;
+        __syncwarp();
+        if (valid) y[r] = ne ? v : Y(0);
+        above += __popc(mask);
+        __syncwarp();
     }
-    // long range: find the row starts inside the tile by searches (each lane
-    // its own W positions), read every moving partial, zero the whole range,
-    // then store the partials in their rows
-    const int32_t Wl = a.L / 32;
-    const int64_t lo = b + (int64_t)lane * Wl;
-    const int64_t hi = (lo + Wl < e) ? lo + Wl : e;
-    int32_t rows[kMaxHeadsPerLane];
-    int nh = 0;
-    for_row_starts<true>(row_ptr, start, stop, lo, hi, [&](int64_t, int32_t r) {
-        if (r < stop && nh < kMaxHeadsPerLane) rows[nh++] = r;
-    });
-    const int incl = warp_inclusive_scan(nh, lane);
-    const int first_s = incl - nh + 1;  // segment index of the lane's first head
-    if (lane == 31 && incl != K) atomicOr(a.err, SSSPMV_DEV_CALIB);
-    Y vals[kMaxHeadsPerLane];
-#pragma unroll
-    for (int i = 0; i < kMaxHeadsPerLane; ++i)
-        if (i < nh) vals[i] = y[start + first_s + i];
-    __syncwarp();
-    for (int64_t r = (int64_t)start + 1 + lane; r < stop; r += 32) y[r] = Y(0);
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < kMaxHeadsPerLane; ++i)
-        if (i < nh) y[rows[i]] = vals[i];
+    if (lane == 0 && above != K) atomicOr(a.err, SSSPMV_DEV_CALIB);
 }
 
 template <class P>
@@ -689,7 +644,7 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
         const int64_t nw = (int64_t)a.nblk_tiles * kCalibWarps;
         for (int64_t t = (int64_t)blk * kCalibWarps + warp; t < a.ntiles; t += nw) {
             const uint32_t info = __ldg(a.tile_info + t);
-            if (info >> 31) repair_dirty_tile<P>(a, t, info, lane);
+            if ((info & kInfoDirty) && !(info & kInfoResolved)) repair_dirty_tile<P>(a, t, info, lane);
         }
         return;
     }

@@ -4,13 +4,11 @@
 
 namespace ssspmv {
 
-#define SSSPMV_F32_SHAPES(X) X(15) X(21) X(27) X(31)
-
 int f32_supported_w(int32_t *out, int cap)
 {
     int n = 0;
 #define X(w) if (n < cap) out[n] = w; ++n;
-    SSSPMV_F32_SHAPES(X)
+    SSSPMV_SHAPES(X)
 #undef X
     return n;
 }
@@ -19,7 +17,7 @@ int f32_resolve(Layout &l, int32_t S_opt)
 {
     switch (l.W) {
 #define X(w) case w: resolve_bunches<F32C, w>(l, S_opt); return SSSPMV_OK;
-        SSSPMV_F32_SHAPES(X)
+        SSSPMV_SHAPES(X)
 #undef X
     default: return SSSPMV_EUNSUPPORTED;
     }
@@ -29,7 +27,7 @@ int f32_run(Call &c)
 {
     switch (c.lay.W) {
 #define X(w) case w: return run_shape<F32C, w>(c);
-        SSSPMV_F32_SHAPES(X)
+        SSSPMV_SHAPES(X)
 #undef X
     default: return SSSPMV_EUNSUPPORTED;
     }

@@ -3,13 +3,11 @@
 
 namespace ssspmv {
 
-#define SSSPMV_F64_SHAPES(X) X(15) X(21) X(27) X(31)
-
 int f64_supported_w(int32_t *out, int cap)
 {
     int n = 0;
 #define X(w) if (n < cap) out[n] = w; ++n;
-    SSSPMV_F64_SHAPES(X)
+    SSSPMV_SHAPES(X)
 #undef X
     return n;
 }
@@ -18,7 +16,7 @@ int f64_resolve(Layout &l, int32_t S_opt)
 {
     switch (l.W) {
 #define X(w) case w: resolve_bunches<F64, w>(l, S_opt); return SSSPMV_OK;
-        SSSPMV_F64_SHAPES(X)
+        SSSPMV_SHAPES(X)
 #undef X
     default: return SSSPMV_EUNSUPPORTED;
     }
@@ -28,7 +26,7 @@ int f64_run(Call &c)
 {
     switch (c.lay.W) {
 #define X(w) case w: return run_shape<F64, w>(c);
-        SSSPMV_F64_SHAPES(X)
+        SSSPMV_SHAPES(X)
 #undef X
     default: return SSSPMV_EUNSUPPORTED;
     }

@@ -39,7 +39,7 @@ class SsspmvError(RuntimeError):
 
 class ssspmv_opts(ctypes.Structure):
     _fields_ = [("W", ctypes.c_int32), ("S", ctypes.c_int32), ("validate", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("timer", ctypes.c_void_p)]
+                ("variant", ctypes.c_int32), ("timer", ctypes.c_void_p)]
 
 
 _L = None
@@ -121,9 +121,12 @@ def _stream(s):
     return s.cuda_stream
 
 
-def make_opts(W: int = 0, S: int = 0, timer=None) -> ssspmv_opts:
+VARIANT_DEFAULT, VARIANT_SPECULATIVE, VARIANT_EXACT = 0, 1, 2
+
+
+def make_opts(W: int = 0, S: int = 0, timer=None, variant: int = 0) -> ssspmv_opts:
     o = ssspmv_opts()
-    o.W, o.S, o.validate, o.reserved = W, S, 0, 0
+    o.W, o.S, o.validate, o.variant = W, S, 0, variant
     o.timer = timer
     return o
 

@@ -32,11 +32,22 @@ def _api():
     return api, ssspmv
 
 
-def check_case(dev, row_ptr, col, val, x, n, W=0, S=0, expect_exact=None):
+def check_case(dev, row_ptr, col, val, x, n, W=0, S=0, expect_exact=None, variant=None):
+    """Runs both dirty-tile variants (speculative + calibration, and exact
+    stores in kernel (b)) unless one is given; returns the last result."""
+    _, C = _api()
+    variants = [C.VARIANT_SPECULATIVE, C.VARIANT_EXACT] if variant is None else [variant]
+    out = None
+    for v in variants:
+        out = _check_one(dev, row_ptr, col, val, x, n, W, S, expect_exact, v)
+    return out
+
+
+def _check_one(dev, row_ptr, col, val, x, n, W, S, expect_exact, variant):
     api, C = _api()
     A = api.to_device(row_ptr, col, val, n, dev)
     xd = torch.as_tensor(x, dtype=torch.float64, device=dev)
-    opts = C.make_opts(W=W, S=S)
+    opts = C.make_opts(W=W, S=S, variant=variant)
     out = api.spmv_f64_debug(A, xd, opts)
     shape = out["shape"]
     L = shape["L"]
@@ -58,7 +69,12 @@ def check_case(dev, row_ptr, col, val, x, n, W=0, S=0, expect_exact=None):
         dirty, nseg = oracle.tile_flags(row_ptr, L, toff)
         info = out["tile_info"]
         assert np.array_equal((info >> 31).astype(np.uint8), dirty)
-        assert np.array_equal((info & 0x7FFFFFFF).astype(np.int32), nseg)
+        assert np.array_equal((info & 0x3FFFFFFF).astype(np.int32), nseg)
+        resolved = ((info >> 30) & 1).astype(np.uint8)
+        if variant == C.VARIANT_EXACT:
+            assert np.array_equal(resolved, dirty)     # every dirty tile resolved in (b)
+        else:
+            assert not resolved.any()
         Sx = shape["S"]
         assert np.array_equal(out["sync_idx"], toff[np.arange(shape["nbunches"]) * Sx])
     return out
@@ -236,7 +252,7 @@ def test_full_size_workloads(dev, name):
     assert np.array_equal(out["tile_offset"], toff)
     dirty, nseg = oracle.tile_flags(A.row_ptr, L, toff)
     assert np.array_equal((out["tile_info"] >> 31).astype(np.uint8), dirty)
-    assert np.array_equal((out["tile_info"] & 0x7FFFFFFF).astype(np.int32), nseg)
+    assert np.array_equal((out["tile_info"] & 0x3FFFFFFF).astype(np.int32), nseg)
     # the descriptor on a sample of tiles spread over the matrix
     idx = np.unique(np.linspace(0, out["shape"]["ntiles"] - 1, 4001).astype(np.int64))
     d = oracle.descriptors(A.row_ptr, L, toff)
