@@ -216,8 +216,8 @@ def run_ours(args):
     Ad = api.to_device(A.row_ptr, A.col, A.val, A.n, dev)
     xd = torch.as_tensor(x, device=dev)
     y = torch.empty(A.m, dtype=torch.float64, device=dev)
-    shape = C.ssspmv_plan_shape(A.m, A.nnz, 8, C.make_opts(W=args.tile_w, S=args.tile_s))
-    ws = api.workspace_for(Ad, C.make_opts(W=args.tile_w, S=args.tile_s), device=dev)
+    shape = C.ssspmv_plan_shape(A.m, A.nnz, 8, C.make_opts(W=args.tile_w, S=args.tile_s, variant=args.variant))
+    ws = api.workspace_for(Ad, C.make_opts(W=args.tile_w, S=args.tile_s, variant=args.variant), device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -227,7 +227,7 @@ def run_ours(args):
         if rc != 0:
             raise C.SsspmvError(rc, "ssspmv_csr_f64")
 
-    plain = C.make_opts(W=args.tile_w, S=args.tile_s)
+    plain = C.make_opts(W=args.tile_w, S=args.tile_s, variant=args.variant)
     for _ in range(args.warmup):
         flush.zero_()
         step(plain)
@@ -237,7 +237,7 @@ def run_ours(args):
     # launching stream
     K = args.steps
     timer = C.ssspmv_timer_create(K)
-    opts_t = C.make_opts(W=args.tile_w, S=args.tile_s, timer=timer)
+    opts_t = C.make_opts(W=args.tile_w, S=args.tile_s, timer=timer, variant=args.variant)
 
     sampler = ClockSampler(local)
     if world > 1:
@@ -324,6 +324,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": args.workload, "m": A.m, "n": A.n, "nnz": A.nnz,
                        "W": shape["W"], "L": shape["L"], "S": shape["S"],
+                       "variant": ["default", "speculative", "exact"][args.variant],
                        "bunches": shape["nbunches"], "bytes_per_step": nbytes,
                        "paper_bytes_per_step": paper_bytes(A.m, A.nnz),
                        "hbm_frac": round(value / world / hbm, 4),
@@ -358,6 +359,8 @@ def main():
     ap.add_argument("--workload", default="stencil160")
     ap.add_argument("--tile-w", type=int, default=0)
     ap.add_argument("--tile-s", type=int, default=0)
+    ap.add_argument("--variant", type=int, default=0,
+                    help="0 default, 1 speculative + calibration, 2 exact stores")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args()
