@@ -54,7 +54,9 @@ __global__ void __launch_bounds__(kPartitionThreads)
         err[1] = 0u;  // bunch ticket of kernel (b)
         tile_offset[ntiles] = m;  // b = nnz: every row pointer is <= nnz
     }
-    for (int64_t r0 = i0; r0 < m; r0 += 4 * stride) {
+    // every lane of a warp runs the same iterations (the ballots need them)
+    const int64_t warp0 = i0 - (threadIdx.x & 31);
+    for (int64_t r0 = i0; warp0 + (r0 - i0) < m; r0 += 4 * stride) {
         int32_t lo[4], hi[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {  // four independent rows in flight
@@ -64,9 +66,23 @@ __global__ void __launch_bounds__(kPartitionThreads)
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            // tiles t with lo <= t*L < hi
-            for (int64_t t = ((uint32_t)lo[u] + (uint32_t)(L - 1)) / (uint32_t)L; t * L < hi[u]; ++t)
-                tile_offset[t] = (int32_t)(r0 + u * stride);
+            // tiles t with lo <= t*L < hi; a row spanning many tiles is
+            // written by the whole warp
+            const int64_t r = r0 + u * stride;
+            const int64_t tlo = ((uint32_t)lo[u] + (uint32_t)(L - 1)) / (uint32_t)L;
+            const int64_t thi = ((uint32_t)hi[u] + (uint32_t)(L - 1)) / (uint32_t)L;
+            const bool longrow = thi - tlo > 8;
+            if (!longrow)
+                for (int64_t t = tlo; t < thi; ++t) tile_offset[t] = (int32_t)r;
+            unsigned lm = __ballot_sync(0xffffffffu, longrow);
+            while (lm) {
+                const int src = __ffs(lm) - 1;
+                lm &= lm - 1;
+                const int64_t a = __shfl_sync(0xffffffffu, tlo, src);
+                const int64_t z = __shfl_sync(0xffffffffu, thi, src);
+                const int32_t rr = (int32_t)__shfl_sync(0xffffffffu, r, src);
+                for (int64_t t = a + (threadIdx.x & 31); t < z; t += 32) tile_offset[t] = rr;
+            }
         }
     }
 }
