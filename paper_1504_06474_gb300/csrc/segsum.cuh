@@ -43,6 +43,10 @@ struct F64 {
     {
         return __shfl_up_sync(FULL, a, d);
     }
+    __device__ static __forceinline__ acc_t shfl(acc_t a, int src)
+    {
+        return __shfl_sync(FULL, a, src);
+    }
     __device__ static __forceinline__ x_t gather(const x_t *x, int32_t c, uint64_t pol)
     {
         return ldg_keep(x + c, pol);
@@ -96,6 +100,10 @@ struct CompF32Traits {
     {
         return CompF32{__shfl_up_sync(FULL, a.s, d), __shfl_up_sync(FULL, a.c, d)};
     }
+    __device__ static __forceinline__ acc_t shfl(acc_t a, int src)
+    {
+        return CompF32{__shfl_sync(FULL, a.s, src), __shfl_sync(FULL, a.c, src)};
+    }
     __device__ static __forceinline__ x_t gather(const x_t *x, int32_t c, uint64_t pol)
     {
         return ldg_keep(x + c, pol);
@@ -130,8 +138,7 @@ struct WarpSmem {
     static constexpr int BAR_OFF = STAGES * STAGE_BYTES;
     static constexpr int DESC_OFF = BAR_OFF + STAGES * 8;
     static constexpr int DESC_WORDS = W + 1;  // one spare word for 64-bit windows
-    static constexpr int SLOT_OFF = (DESC_OFF + DESC_WORDS * 4 + 15) & ~15;
-    static constexpr int BYTES = (SLOT_OFF + 32 + 127) & ~127;
+    static constexpr int BYTES = (DESC_OFF + DESC_WORDS * 4 + 127) & ~127;
 };
 
 // Warps per block (B) and blocks per SM maximising resident warps per SM for
@@ -215,8 +222,6 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
     unsigned char *base = smem_raw + warp * SM::BYTES;
     uint64_t *bar = reinterpret_cast<uint64_t *>(base + SM::BAR_OFF);
     uint32_t *desc = reinterpret_cast<uint32_t *>(base + SM::DESC_OFF);
-    A *slot_f = reinterpret_cast<A *>(base + SM::SLOT_OFF);           // bunch-first partial
-    A *slot_carry = reinterpret_cast<A *>(base + SM::SLOT_OFF + 16);  // transmitter
 
     const int64_t nwarps = (int64_t)gridDim.x * B;
     int64_t cur = (int64_t)blockIdx.x * B + warp;  // bunch being processed
@@ -294,7 +299,8 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
     while (true) {
         const int64_t t0 = cur * S, t1 = bunch_end(cur);
         const int32_t rF = start;  // the bunch's first row
-        A carry = P::zero();
+        A carry = P::zero();   // transmitter (warp-uniform)
+        A F = P::zero();       // the bunch's first segment (warp-uniform)
         A G = P::zero();
         bool hasG = false;
 
@@ -327,7 +333,7 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
 
             // ---- wait for this tile's val/col
             unsigned char *st = stage_ptr(s);
-            const V *vs = reinterpret_cast<const V *>(st);
+            const V *__restrict__ vs = reinterpret_cast<const V *>(st);
             const int32_t *cs = reinterpret_cast<const int32_t *>(st + SM::VAL_REGION);
             if (!mbar_wait_bounded(&bar[s], par)) {
                 if (lane == 0) atomicOr(a.err, SSSPMV_DEV_TIMEOUT);
@@ -438,9 +444,12 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
             // synchronizer slot (the bunch's first segment), to its
             // speculative row start + sidx (Alg. 1), or -- exact stores on a
             // dirty tile -- to the row that starts at hpos
+            A fval = P::zero();  // the bunch-first partial, held by the lane that made it
+            bool fhave = false;
             auto emit = [&](int sidx, A v, int hpos) {
                 if (sidx == 0 && start == rF) {
-                    *slot_f = v;
+                    fval = v;
+                    fhave = true;
                 } else {
                     const int64_t row = resolve ? (hpos <= 0 ? (int64_t)start : (int64_t)rowmap[hpos])
                                                 : (int64_t)start + sidx;
@@ -520,9 +529,9 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
             if (has && lane > 0) emit(idx0 - 1, P::add(Cprev, pre), prevpos);
             // the tile's last segment: stored, or carried if row `stop` goes on
             if (lane == 31) {
-                *slot_carry = C;
                 if (nseg == 1 && start == rF) {
-                    *slot_f = C;  // still the bunch's first segment
+                    fval = C;  // still the bunch's first segment
+                    fhave = true;
                 } else if (cont) {
                     if (t == t1 - 1) {  // continues into the next bunch
                         G = C;
@@ -535,8 +544,11 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
             if (lane == 0)
                 a.tile_info[t] = (uint32_t)nseg | (dirty ? kInfoDirty : 0u) |
                                  (resolve ? kInfoResolved : 0u);
-            __syncwarp();
-            carry = *slot_carry;
+            carry = P::shfl(C, 31);
+            if (start == rF) {  // exactly one lane made segment 0 of this tile
+                const unsigned fm = __ballot_sync(FULL, fhave);
+                F = P::shfl(fval, fm ? __ffs(fm) - 1 : 0);
+            }
             ++q_con;
             issue_next();  // the stage just consumed takes the next copy
             start = start_nx;
@@ -545,8 +557,6 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
             pr_chunk2 = pr_nx2;
         }
         // ---- synchronizer record of the bunch; its sums are finished in FP64
-        __syncwarp();
-        const A F = *slot_f;
         if (lane == 31) {
             a.sync_idx[cur] = rF;
             static_cast<double *>(a.sync_val)[cur] = P::to_f64(F);
