@@ -451,9 +451,10 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
                     fval = v;
                     fhave = true;
                 } else {
-                    const int64_t row = resolve ? (hpos <= 0 ? (int64_t)start : (int64_t)rowmap[hpos])
+                    const int64_t row = resolve ? (hpos <= 0 ? (int64_t)start
+                                                         : (int64_t)rowmap[hpos < L ? hpos : 0])
                                                 : (int64_t)start + sidx;
-                    if (row < a.m) y[row] = P::out(v);
+                    if (row >= 0 && row < a.m) y[row] = P::out(v);
                     else atomicOr(a.err, SSSPMV_DEV_RANGE);
                 }
             };
