@@ -17,6 +17,7 @@
 // 8 bytes are still a multiple of 16 bytes for the bulk copies.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -240,11 +241,20 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
 
     auto bunch_end = [&](int64_t bb) { return (bb * S + S < a.ntiles) ? bb * S + S : a.ntiles; };
     int64_t nxt = -1;  // the warp's next bunch, once claimed (warp-uniform)
+    uint32_t tk = 0;   // lane 0: a ticket requested ahead of its use
+    bool tk_pending = false;
+    // request the next ticket early; its value is read only when needed, so
+    // the atomic's round trip overlaps the current bunch
+    auto request_ticket = [&]() {
+        if (nxt >= 0 || tk_pending) return;
+        if (lane == 0) tk = atomicAdd(a.ticket, 1u);
+        tk_pending = true;
+    };
     auto claim_next = [&]() {
         if (nxt >= 0) return;
-        uint32_t v = 0;
-        if (lane == 0) v = atomicAdd(a.ticket, 1u);
-        nxt = nwarps + (int64_t)__shfl_sync(FULL, v, 0);
+        request_ticket();
+        tk_pending = false;
+        nxt = nwarps + (int64_t)__shfl_sync(FULL, tk, 0);
     };
 
     auto stage_ptr = [&](uint32_t s) { return base + s * SM::STAGE_BYTES; };
@@ -297,6 +307,7 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
     constexpr int HB = W - HA;       // entries [0, HA) and [HA, W)
 
     while (true) {
+        request_ticket();
         const int64_t t0 = cur * S, t1 = bunch_end(cur);
         const int32_t rF = start;  // the bunch's first row
         A carry = P::zero();   // transmitter (warp-uniform)
@@ -355,11 +366,17 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
 
             // ---- gathers of x for the lane's W entries (Alg. 1 products),
             // issued before the descriptor work so their latency overlaps it
+            const bool full = len == L;  // all tiles but the last
             X xv[W];
+            if (full) {
 #pragma unroll
-            for (int j = 0; j < W; ++j) {
-                const int k = lane * W + j;
-                xv[j] = (k < len) ? P::gather(x, cs[k], pol_keep) : X(0);
+                for (int j = 0; j < W; ++j) xv[j] = P::gather(x, cs[lane * W + j], pol_keep);
+            } else {
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    const int k = lane * W + j;
+                    xv[j] = (k < len) ? P::gather(x, cs[k], pol_keep) : X(0);
+                }
             }
 
             // ---- segment descriptor built on chip from row_ptr[start..stop]
@@ -463,30 +480,68 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
             // two interleaved chains; a head closes the open segment (the
             // part before a chain's first head belongs to an earlier segment)
             A accA = P::zero(), preA = P::zero(), accB = P::zero(), preB = P::zero();
-            int curA = idx0 - 1, curB = idx0 + cA - 1;
             int posA = -1, posB = -1;  // tile position of each chain's last head
+            const A initA = (lane == 0) ? cin : P::zero();  // lane 0's forced head takes the transmitter
+            // fast path: every chain of the warp holds at most one head, so a
+            // head only splits its chain into the part before it and after it
+            // (selects, no branches, no stores inside the loop)
+            const bool fast = __all_sync(FULL, cA <= 1 && cB <= 1);
+            auto fma_fast = [&](auto full_tag) {
+                constexpr bool FT = decltype(full_tag)::value;
+                const int hA = cA ? __ffs(hbA) - 1 : -1;
+                const int hB = cB ? __ffs(hbB) - 1 : -1;
 #pragma unroll
-            for (int i = 0; i < HA; ++i) {
-                const int kA = lane * W + i;
-                if ((hbA >> i) & 1u) {
-                    if (curA >= idx0) emit(curA, accA, posA);
-                    else preA = accA;
-                    ++curA;
-                    posA = kA;
-                    accA = (i == 0 && lane == 0) ? cin : P::zero();
-                }
-                if (kA < len) accA = P::fma(vs[kA], xv[i], accA);
-                if (i < HB) {
-                    const int kB = lane * W + HA + i;
-                    if ((hbB >> i) & 1u) {
-                        if (curB >= idx0 + cA) emit(curB, accB, posB);
-                        else preB = accB;
-                        ++curB;
-                        posB = kB;
-                        accB = P::zero();
+                for (int i = 0; i < HA; ++i) {
+                    const int kA = lane * W + i;
+                    const bool hdA = i == hA;
+                    preA = hdA ? accA : preA;
+                    accA = hdA ? initA : accA;
+                    if (FT || kA < len) accA = P::fma(vs[kA], xv[i], accA);
+                    if (i < HB) {
+                        const int kB = lane * W + HA + i;
+                        const bool hdB = i == hB;
+                        preB = hdB ? accB : preB;
+                        accB = hdB ? P::zero() : accB;
+                        if (FT || kB < len) accB = P::fma(vs[kB], xv[HA + i], accB);
                     }
-                    if (kB < len) accB = P::fma(vs[kB], xv[HA + i], accB);
                 }
+                posA = cA ? lane * W + hA : -1;
+                posB = cB ? lane * W + HA + hB : -1;
+            };
+            // general path: any number of heads per chain
+            auto fma_general = [&](auto full_tag) {
+                constexpr bool FT = decltype(full_tag)::value;
+                int curA = idx0 - 1, curB = idx0 + cA - 1;
+#pragma unroll
+                for (int i = 0; i < HA; ++i) {
+                    const int kA = lane * W + i;
+                    if ((hbA >> i) & 1u) {
+                        if (curA >= idx0) emit(curA, accA, posA);
+                        else preA = accA;
+                        ++curA;
+                        posA = kA;
+                        accA = (i == 0) ? initA : P::zero();
+                    }
+                    if (FT || kA < len) accA = P::fma(vs[kA], xv[i], accA);
+                    if (i < HB) {
+                        const int kB = lane * W + HA + i;
+                        if ((hbB >> i) & 1u) {
+                            if (curB >= idx0 + cA) emit(curB, accB, posB);
+                            else preB = accB;
+                            ++curB;
+                            posB = kB;
+                            accB = P::zero();
+                        }
+                        if (FT || kB < len) accB = P::fma(vs[kB], xv[HA + i], accB);
+                    }
+                }
+            };
+            if (fast) {
+                if (full) fma_fast(std::true_type{});
+                else fma_fast(std::false_type{});
+            } else {
+                if (full) fma_general(std::true_type{});
+                else fma_general(std::false_type{});
             }
             if (cA == 0) preA = accA;  // chain totals when a chain has no head
             if (cB == 0) preB = accB;
