@@ -32,9 +32,8 @@
  *     in int32.  Column order inside a row is free; duplicates are summed.
  *   - `val` and `col_idx` must be 16-byte aligned (they are streamed by bulk
  *     asynchronous copies); x and y need only natural alignment.
- *   - Column indices must lie in [0, n); with opts->validate == 0 an
- *     out-of-range column is undefined behaviour (call ssspmv_validate_csr
- *     first for untrusted input).
+ *   - Column indices must lie in [0, n); an out-of-range column is undefined
+ *     behaviour (call ssspmv_validate_csr first for untrusted input).
  *   - Return value: SSSPMV_OK (0) or a negative code; nothing is launched
  *     when a host-side check fails.  No C++ exception crosses the ABI.
  *   - The same input gives bit-identical y on every run (no floating-point
@@ -57,6 +56,10 @@ extern "C" {
 #define SSSPMV_EDEVICE      -4  /* a kernel reported an inconsistency or a timed-out wait */
 #define SSSPMV_EUNSUPPORTED -5  /* tile shape not compiled in this build */
 #define SSSPMV_ETOOLARGE    -6  /* problem needs more scratch than ssspmv_csr_f64_noalloc has */
+
+/* Largest m and nnz accepted (larger values return SSSPMV_EINVAL): the
+ * kernels index rows and entries in 32-bit integers with 256 of headroom. */
+#define SSSPMV_MAX_DIM (2147483647 - 256)
 
 /* Device error bits written by the kernels into the workspace (read with
  * ssspmv_device_status). */
@@ -81,11 +84,15 @@ extern "C" {
  * only what you need; a NULL opts pointer means all defaults. */
 typedef struct ssspmv_opts {
     int32_t W;         /* entries per lane (odd, see ssspmv_supported_w); L = 32*W.
-                          0 = pick from the mean row length nnz/m */
-    int32_t S;         /* tiles per thread-bunch (warp); 0 = 4.  Bunches are handed
-                          to a persistent grid of warps in order, each warp taking
-                          the next unclaimed bunch */
-    int32_t validate;  /* reserved, must be 0 (use ssspmv_validate_csr) */
+                          0 = the shortest compiled tile */
+    int32_t S;         /* tiles per thread-bunch (warp); 0 = 4.  Each warp of a
+                          persistent grid first takes an even contiguous share of
+                          3/4 of the bunches, then single bunches from a counter */
+    int32_t block_warps; /* warps per block of the segmented-sum kernel (one block
+                          per SM).  0 = automatic: all that fit in shared memory
+                          when the mean row length nnz/m is at least 20, else as
+                          many as leave about 56 KB of L1 for the x gathers;
+                          values above the most that fit are lowered to it */
     int32_t variant;   /* SSSPMV_VARIANT_*: how tiles holding empty rows are stored */
     void   *timer;     /* optional ssspmv_timer*: the call records its kernel
                           boundaries into the timer's next slot; NULL = none */

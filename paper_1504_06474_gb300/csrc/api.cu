@@ -84,13 +84,15 @@ static int resolve_w(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_opt
             if (ws[i] == o->W) { *W = o->W; return SSSPMV_OK; }
         return o->W < 0 ? SSSPMV_EINVAL : SSSPMV_EUNSUPPORTED;
     }
-    const double mean = m > 0 ? (double)nnz / (double)m : 0.0;
+    // default: the shortest compiled tile.  Shorter tiles leave room for more
+    // resident warps per SM, which hides the latency of the per-tile work
+    // (descriptor, gathers, cross-lane sums) better than longer tiles
+    // amortise it; this held on stencil and power-law matrices alike.
+    (void)m;
+    (void)nnz;
     int best = ws[0];
-    double bd = 1e300;
-    for (int i = 0; i < n; ++i) {
-        const double d = std::fabs((double)ws[i] - mean);
-        if (d < bd) { bd = d; best = ws[i]; }
-    }
+    for (int i = 1; i < n; ++i)
+        if (ws[i] < best) best = ws[i];
     *W = best;
     return SSSPMV_OK;
 }
@@ -99,7 +101,9 @@ static int resolve_w(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_opt
 static int make_layout(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_opts *o, Layout &l)
 {
     if (m < 0 || nnz < 0) return SSSPMV_EINVAL;
-    if (o && (o->S < 0 || o->validate != 0 || o->variant < 0 || o->variant > 2))
+    // the kernels index rows and entries in 32 bits with up to 256 of headroom
+    if (m > SSSPMV_MAX_DIM || nnz > SSSPMV_MAX_DIM) return SSSPMV_EINVAL;
+    if (o && (o->S < 0 || o->block_warps < 0 || o->variant < 0 || o->variant > 2))
         return SSSPMV_EINVAL;
     int32_t W = 0;
     int rc = resolve_w(m, nnz, val_bytes, o, &W);
@@ -179,6 +183,7 @@ static int run_call(int32_t val_bytes, int32_t m, int32_t n, int32_t nnz,
     c.dbg_desc = dbg_desc;
     c.dbg_yspec = dbg_yspec;
     c.exact = (opts && opts->variant == SSSPMV_VARIANT_EXACT) ? 1 : 0;
+    c.block_warps = opts ? opts->block_warps : 0;
     return pr->run(c);
 }
 

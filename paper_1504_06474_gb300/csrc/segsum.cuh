@@ -30,7 +30,7 @@ namespace ssspmv {
 // precision traits
 
 struct F64 {
-    static constexpr int kMaxWarps = 16;  // 128 registers per thread
+    static constexpr int kMaxWarps = 32;  // shared memory decides
     using val_t = double;
     using x_t = double;
     using y_t = double;
@@ -139,7 +139,8 @@ struct WarpSmem {
     static constexpr int BAR_OFF = STAGES * STAGE_BYTES;
     static constexpr int DESC_OFF = BAR_OFF + STAGES * 8;
     static constexpr int DESC_WORDS = W + 1;  // one spare word for 64-bit windows
-    static constexpr int BYTES = (DESC_OFF + DESC_WORDS * 4 + 127) & ~127;
+    static constexpr int SLOT_OFF = (DESC_OFF + DESC_WORDS * 4 + 15) & ~15;
+    static constexpr int BYTES = (SLOT_OFF + 32 + 127) & ~127;
 };
 
 // Warps per block (B) and blocks per SM maximising resident warps per SM for
@@ -188,7 +189,6 @@ struct SegsumArgs {
     int64_t ntiles;
     int64_t nbunches;
     int32_t S;
-    int32_t exact;       // 1: dirty tiles store their partials in their true rows
 };
 
 // tile_info layout: bit 31 dirty, bit 30 dirty and resolved by kernel (b),
@@ -198,14 +198,64 @@ constexpr uint32_t kInfoResolved = 0x40000000u;
 constexpr uint32_t kInfoSegMask = 0x3fffffffu;
 
 // ---------------------------------------------------------------------------
-// kernel (b): a thread-bunch (warp) processes S consecutive tiles, carrying the
-// transmitter from tile to tile.  Bunches are handed to a persistent grid of
-// warps: warp g starts with bunch g, then takes the next unclaimed bunch from
-// a ticket counter -- the dynamic assignment of the paper's thread-groups to
-// cores, without refilling the copy pipeline at every bunch (the copies of a
-// warp's next bunch are issued while it finishes the current one).
+// descriptor scan of rows [rb0, stop] for tiles over many (mostly empty) rows,
+// four chunks of 32 rows per round trip.  Kept out of line: the call is rare
+// and the loop then keeps its loads in flight with registers of its own
+// instead of competing with the tile's gathered x.  Returns bit 0: an empty
+// row in [rb0, stop); bit 1: row `stop` starts inside the tile.  With exact
+// stores it also writes the position-to-row map and zeroes the empty rows.
+template <bool EXACT, class Y>
+__device__ __noinline__ uint32_t scan_rows_long(const int32_t *__restrict__ row_ptr, int32_t m,
+                                                int32_t rb0, int32_t stop, int32_t b, int32_t len,
+                                                uint32_t *desc, int32_t *rowmap, Y *y)
+{
+    constexpr int CH = 4;
+    const int lane = threadIdx.x & 31;
+    const int32_t e = b + len;
+    uint32_t flags = 0;
+    for (int32_t rb = rb0; rb <= stop; rb += 32 * CH) {
+        int32_t prs[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const int32_t r = rb + 32 * u + lane;
+            prs[u] = __ldg(row_ptr + (r < m ? r : m));
+        }
+        int32_t tail = 0;
+        if (lane == 31 && rb + 32 * CH - 1 < stop) tail = __ldg(row_ptr + rb + 32 * CH);
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const int32_t r = rb + 32 * u + lane;
+            const int32_t pr = prs[u];
+            const int32_t nlead = __shfl_sync(FULL, prs[u < CH - 1 ? u + 1 : CH - 1], 0);
+            int32_t nx = __shfl_down_sync(FULL, pr, 1);
+            if (lane == 31) nx = (u < CH - 1) ? nlead : tail;
+            if (r <= stop) {
+                const int32_t k = pr - b;
+                if (k >= 0 && k < len) atomicOr(&desc[k >> 5], 1u << (k & 31));
+                if (r < stop) {
+                    if (nx == pr) {
+                        flags |= 1u;
+                        if (EXACT) y[r] = Y(0);
+                    } else if (EXACT && k > 0) {
+                        rowmap[k] = r;
+                    }
+                }
+                if (r == stop && pr < e) flags |= 2u;
+            }
+        }
+    }
+    return flags;
+}
 
-template <class P, int W, int B, int MINB>
+// ---------------------------------------------------------------------------
+// kernel (b): a thread-bunch (warp) processes S consecutive tiles, carrying the
+// transmitter from tile to tile.  Bunches go to a persistent grid of warps:
+// warp g first streams a contiguous range of bunches (3/4 of all bunches are
+// split evenly this way, so the copy stream of a warp runs through memory in
+// order), then takes the remaining bunches one at a time from a ticket
+// counter, which evens out bunches that cost more (tiles over many rows).
+
+template <class P, int W, int B, int MINB, bool EXACT>
 __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a)
 {
     using V = typename P::val_t;
@@ -223,10 +273,25 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
     unsigned char *base = smem_raw + warp * SM::BYTES;
     uint64_t *bar = reinterpret_cast<uint64_t *>(base + SM::BAR_OFF);
     uint32_t *desc = reinterpret_cast<uint32_t *>(base + SM::DESC_OFF);
+    A *slot_f = reinterpret_cast<A *>(base + SM::SLOT_OFF);           // bunch-first partial
+    A *slot_carry = reinterpret_cast<A *>(base + SM::SLOT_OFF + 16);  // transmitter
 
-    const int64_t nwarps = (int64_t)gridDim.x * B;
-    int64_t cur = (int64_t)blockIdx.x * B + warp;  // bunch being processed
-    if (cur >= a.nbunches) return;
+    // tiles, bunches, rows and positions all fit in 32 bits (the host
+    // rejects m or nnz within 256 of the int32 limit)
+    const int32_t nb = (int32_t)a.nbunches;
+    const int32_t ntiles = (int32_t)a.ntiles;
+    // blocks may be launched with fewer than B warps (more L1 per warp)
+    const int32_t bw = (int32_t)(blockDim.x >> 5);
+    const int32_t nwarps = (int32_t)gridDim.x * bw;
+    const int32_t g = (int32_t)blockIdx.x * bw + warp;
+    if (g >= nb) return;
+    // static share: bunches [g*Q, (g+1)*Q); bunches from nwarps*Q on are
+    // handed out by ticket
+    int32_t Q = (int32_t)((3 * (int64_t)nb) / (4 * (int64_t)nwarps));
+    if (Q < 1) Q = 1;
+    const int32_t static_end = (g + 1) * Q;
+    const int32_t dyn_base = nwarps * Q;
+    int32_t cur = g * Q;
 
     const V *__restrict__ val = static_cast<const V *>(a.val);
     const X *__restrict__ x = static_cast<const X *>(a.x);
@@ -234,34 +299,36 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
     const int32_t *__restrict__ row_ptr = a.row_ptr;
     const int32_t *__restrict__ col = a.col;
     const int32_t nnz = a.nnz;
-    const int64_t S = a.S;
+    const int32_t S = a.S;
 
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
 
-    auto bunch_end = [&](int64_t bb) { return (bb * S + S < a.ntiles) ? bb * S + S : a.ntiles; };
-    int64_t nxt = -1;  // the warp's next bunch, once claimed (warp-uniform)
+    auto bunch_end = [&](int32_t bb) { return (bb * S + S < ntiles) ? bb * S + S : ntiles; };
+    int32_t nxt = -1;  // the warp's next bunch, once known (warp-uniform)
     uint32_t tk = 0;   // lane 0: a ticket requested ahead of its use
     bool tk_pending = false;
-    // request the next ticket early; its value is read only when needed, so
-    // the atomic's round trip overlaps the current bunch
-    auto request_ticket = [&]() {
-        if (nxt >= 0 || tk_pending) return;
+    auto request_ticket = [&]() {  // the atomic's round trip overlaps the bunch
+        if (nxt >= 0 || tk_pending || cur + 1 < static_end) return;
         if (lane == 0) tk = atomicAdd(a.ticket, 1u);
         tk_pending = true;
     };
     auto claim_next = [&]() {
         if (nxt >= 0) return;
+        if (cur + 1 < static_end) {
+            nxt = cur + 1;
+            return;
+        }
         request_ticket();
         tk_pending = false;
-        nxt = nwarps + (int64_t)__shfl_sync(FULL, tk, 0);
+        nxt = dyn_base + (int32_t)__shfl_sync(FULL, tk, 0);
     };
 
     auto stage_ptr = [&](uint32_t s) { return base + s * SM::STAGE_BYTES; };
     // bulk copies of tile tt into stage s (lane 0 only)
-    auto issue = [&](int64_t tt, uint32_t s) {
-        const int64_t b = tt * L;
-        const int32_t len = (int32_t)((nnz - b < L) ? nnz - b : L);
+    auto issue = [&](int32_t tt, uint32_t s) {
+        const int32_t b = tt * L;
+        const int32_t len = (nnz - b < L) ? nnz - b : L;
         const uint32_t vb = ((uint32_t)len * (uint32_t)sizeof(V)) & ~15u;
         const uint32_t cb = ((uint32_t)len * 4u) & ~15u;
         mbar_arrive_expect_tx(&bar[s], vb + cb);
@@ -270,16 +337,16 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
     };
     // the copy stream runs at most STAGES tiles ahead, into at most the next
     // bunch (warp-uniform: every lane calls it)
-    int64_t iss_b = cur, iss_t = cur * S;
+    int32_t iss_b = cur, iss_t = cur * S;
     uint32_t q_iss = 0, q_con = 0;  // tiles issued / consumed by this warp
     auto issue_next = [&]() {
-        if (iss_b >= a.nbunches) return;
+        if (iss_b >= nb) return;
         if (iss_t >= bunch_end(iss_b)) {
             if (iss_b != cur) return;
             claim_next();
             iss_b = nxt;
             iss_t = nxt * S;
-            if (iss_b >= a.nbunches) return;
+            if (iss_b >= nb) return;
         }
         if (lane == 0) {
             fence_proxy_async_smem();
@@ -300,27 +367,24 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
     // one tile ahead (rows past m read row_ptr[m])
     int32_t start = __ldg(a.tile_offset + cur * S);
     int32_t stop = __ldg(a.tile_offset + cur * S + 1);
-    int32_t pr_chunk = __ldg(row_ptr + (start + lane < a.m ? start + lane : a.m));
-    int32_t pr_chunk2 = __ldg(row_ptr + (start + 32 + lane < a.m ? start + 32 + lane : a.m));
-
-    constexpr int HA = (W + 1) / 2;  // each lane's run is two FMA chains:
-    constexpr int HB = W - HA;       // entries [0, HA) and [HA, W)
+    auto rp_at = [&](int32_t r) { return __ldg(row_ptr + (r < a.m ? r : a.m)); };
+    int32_t pr_chunk = rp_at(start + lane);
+    int32_t pr_chunk2 = rp_at(start + 32 + lane);
 
     while (true) {
         request_ticket();
-        const int64_t t0 = cur * S, t1 = bunch_end(cur);
+        const int32_t t0 = cur * S, t1 = bunch_end(cur);
         const int32_t rF = start;  // the bunch's first row
-        A carry = P::zero();   // transmitter (warp-uniform)
-        A F = P::zero();       // the bunch's first segment (warp-uniform)
+        A carry = P::zero();
         A G = P::zero();
         bool hasG = false;
 
-        for (int64_t t = t0; t < t1; ++t) {
+        for (int32_t t = t0; t < t1; ++t) {
             const uint32_t s = q_con % STAGES;
             const uint32_t par = (q_con / STAGES) & 1u;
-            const int64_t b = t * L;
-            const int32_t len = (int32_t)((nnz - b < L) ? nnz - b : L);
-            const int64_t e = b + len;
+            const int32_t b = t * L;
+            const int32_t len = (nnz - b < L) ? nnz - b : L;
+            const int32_t e = b + len;
 
             // ---- prefetch the next tile's rows (the next bunch's first tile
             // after the last one)
@@ -330,7 +394,7 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
                 stop_nx = __ldg(a.tile_offset + t + 2);
             } else {
                 claim_next();
-                if (nxt < a.nbunches) {
+                if (nxt < nb) {
                     start_nx = __ldg(a.tile_offset + nxt * S);
                     stop_nx = __ldg(a.tile_offset + nxt * S + 1);
                 } else {
@@ -338,13 +402,13 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
                 }
             }
             if (have_nx) {
-                pr_nx = __ldg(row_ptr + (start_nx + lane < a.m ? start_nx + lane : a.m));
-                pr_nx2 = __ldg(row_ptr + (start_nx + 32 + lane < a.m ? start_nx + 32 + lane : a.m));
+                pr_nx = rp_at(start_nx + lane);
+                pr_nx2 = rp_at(start_nx + 32 + lane);
             }
 
             // ---- wait for this tile's val/col
             unsigned char *st = stage_ptr(s);
-            const V *__restrict__ vs = reinterpret_cast<const V *>(st);
+            const V *vs = reinterpret_cast<const V *>(st);
             const int32_t *cs = reinterpret_cast<const int32_t *>(st + SM::VAL_REGION);
             if (!mbar_wait_bounded(&bar[s], par)) {
                 if (lane == 0) atomicOr(a.err, SSSPMV_DEV_TIMEOUT);
@@ -359,24 +423,20 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
                 const int32_t vdone =
                     (int32_t)((((uint32_t)len * (uint32_t)sizeof(V)) & ~15u) / sizeof(V));
                 const int32_t cdone = (int32_t)((((uint32_t)len * 4u) & ~15u) / 4u);
-                for (int32_t k = vdone + lane; k < len; k += 32) vw[k] = val[b + k];
-                for (int32_t k = cdone + lane; k < len; k += 32) cw[k] = col[b + k];
+                // entries past len read as val 0, col 0: the loops below then
+                // need no bounds checks (adding 0 * x[0] leaves every sum as is)
+                for (int32_t k = vdone + lane; k < L; k += 32) vw[k] = (k < len) ? val[b + k] : V(0);
+                for (int32_t k = cdone + lane; k < L; k += 32) cw[k] = (k < len) ? col[b + k] : 0;
                 __syncwarp();
             }
 
             // ---- gathers of x for the lane's W entries (Alg. 1 products),
             // issued before the descriptor work so their latency overlaps it
-            const bool full = len == L;  // all tiles but the last
             X xv[W];
-            if (full) {
 #pragma unroll
-                for (int j = 0; j < W; ++j) xv[j] = P::gather(x, cs[lane * W + j], pol_keep);
-            } else {
-#pragma unroll
-                for (int j = 0; j < W; ++j) {
-                    const int k = lane * W + j;
-                    xv[j] = (k < len) ? P::gather(x, cs[k], pol_keep) : X(0);
-                }
+            for (int j = 0; j < W; ++j) {
+                const int k = lane * W + j;
+                xv[j] = P::gather(x, cs[k], pol_keep);
             }
 
             // ---- segment descriptor built on chip from row_ptr[start..stop]
@@ -386,61 +446,48 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
             // With exact stores, a map from tile position to the non-empty
             // row starting there goes into the stage's column region (free
             // once the gathers above are issued) and empty rows are zeroed.
-            const bool exact = a.exact != 0;
             int32_t *rowmap = reinterpret_cast<int32_t *>(st + SM::VAL_REGION);
             if (lane <= W) desc[lane] = 0u;
             __syncwarp();
             bool dirty = false, cont = false, raw0 = false;
-            auto scan_row = [&](int64_t r, int32_t pr, int32_t nx) {
+            auto scan_row = [&](int32_t r, int32_t pr, int32_t nx) {
                 if (r > stop) return;
-                const int64_t k = (int64_t)pr - b;
+                const int32_t k = pr - b;
                 if (k >= 0 && k < len) atomicOr(&desc[k >> 5], 1u << (k & 31));
                 if (r < stop) {
                     if (nx == pr) {
                         dirty = true;
-                        if (exact) y[r] = Y(0);  // r > start: row `start` is never empty
-                    } else if (exact && k > 0) {
+                        if (EXACT) y[r] = Y(0);  // r > start: row `start` is never empty
+                    } else if (EXACT && k > 0) {
                         rowmap[k] = (int32_t)r;
                     }
                 }
                 if (r == start && k == 0) raw0 = true;
-                if (r == stop && (int64_t)pr < e) cont = true;
+                if (r == stop && pr < e) cont = true;
             };
             {
-                // the first two chunks of 32 rows were loaded one tile ahead
-                const int32_t head2 = __shfl_sync(FULL, pr_chunk2, 0);
+                // rows start .. start+63 were loaded one tile ahead
                 int32_t nx = __shfl_down_sync(FULL, pr_chunk, 1);
-                if (lane == 31) nx = head2;
-                scan_row((int64_t)start + lane, pr_chunk, nx);
-                if ((int64_t)start + 32 <= stop) {
-                    nx = __shfl_down_sync(FULL, pr_chunk2, 1);
-                    if (lane == 31 && (int64_t)start + 63 < stop) nx = __ldg(row_ptr + start + 64);
-                    scan_row((int64_t)start + 32 + lane, pr_chunk2, nx);
-                }
-                // longer row ranges: four chunks per round trip
-                for (int64_t rb = (int64_t)start + 64; rb <= stop; rb += 128) {
-                    int32_t prs[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int64_t r = rb + 32 * u + lane;
-                        prs[u] = __ldg(row_ptr + (r < a.m ? r : a.m));
-                    }
-                    int32_t tail = 0;
-                    if (lane == 31 && rb + 127 < stop) tail = __ldg(row_ptr + rb + 128);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int32_t nlead = __shfl_sync(FULL, prs[u < 3 ? u + 1 : 3], 0);
-                        int32_t n2 = __shfl_down_sync(FULL, prs[u], 1);
-                        if (lane == 31) n2 = (u < 3) ? nlead : tail;
-                        scan_row(rb + 32 * u + lane, prs[u], n2);
-                    }
+                const int32_t c2 = __shfl_sync(FULL, pr_chunk2, 0);
+                if (lane == 31) nx = c2;
+                scan_row(start + lane, pr_chunk, nx);
+            }
+            if (start + 32 <= stop) {
+                int32_t nx = __shfl_down_sync(FULL, pr_chunk2, 1);
+                if (lane == 31 && start + 63 < stop) nx = rp_at(start + 64);
+                scan_row(start + 32 + lane, pr_chunk2, nx);
+                if (start + 64 <= stop) {  // long row ranges
+                    const uint32_t f = scan_rows_long<EXACT, Y>(row_ptr, a.m, start + 64, stop, b,
+                                                                len, desc, rowmap, y);
+                    dirty |= (f & 1u) != 0;
+                    cont |= (f & 2u) != 0;
                 }
             }
             dirty = __any_sync(FULL, dirty);
             cont = __any_sync(FULL, cont);
             raw0 = __any_sync(FULL, raw0);
             __syncwarp();
-            const bool resolve = exact && dirty;
+            const bool resolve = EXACT && dirty;
             const int bit0 = lane * W;
             const uint64_t win =
                 ((uint64_t)desc[(bit0 >> 5) + 1] << 32) | (uint64_t)desc[bit0 >> 5];
@@ -449,108 +496,60 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
             if (lane == 0) hb |= 1u;  // each tile opens with a segment (Sec. 3.2)
 
             // ---- compact indices: exclusive scan of head counts (y_index)
-            const uint32_t hbA = hb & ((1u << HA) - 1u), hbB = hb >> HA;
-            const int cA = __popc(hbA), cB = __popc(hbB);
-            const int c = cA + cB;
+            const int c = __popc(hb);
             const int incl = warp_inclusive_scan(c, lane);
             const int idx0 = incl - c;
             const int nseg = __shfl_sync(FULL, incl, 31);
             const A cin = (raw0 || t == t0) ? P::zero() : carry;  // transmitter
 
-            // segment sidx, whose head is at tile position hpos, goes to the
-            // synchronizer slot (the bunch's first segment), to its
-            // speculative row start + sidx (Alg. 1), or -- exact stores on a
-            // dirty tile -- to the row that starts at hpos
-            A fval = P::zero();  // the bunch-first partial, held by the lane that made it
-            bool fhave = false;
+            // segment sidx goes to the synchronizer slot (the bunch's first
+            // segment), to its speculative row start + sidx (Alg. 1), or --
+            // exact stores on a dirty tile -- to the row that starts at its
+            // head position hpos
             auto emit = [&](int sidx, A v, int hpos) {
                 if (sidx == 0 && start == rF) {
-                    fval = v;
-                    fhave = true;
+                    *slot_f = v;
                 } else {
-                    const int64_t row = resolve ? (hpos <= 0 ? (int64_t)start
-                                                         : (int64_t)rowmap[hpos < L ? hpos : 0])
-                                                : (int64_t)start + sidx;
+                    int32_t row = start + sidx;
+                    if (EXACT && resolve) row = hpos <= 0 ? start : rowmap[hpos < L ? hpos : 0];
                     if (row >= 0 && row < a.m) y[row] = P::out(v);
                     else atomicOr(a.err, SSSPMV_DEV_RANGE);
                 }
             };
 
-            // ---- per-lane sequential segmented sum, one FMA per entry, as
-            // two interleaved chains; a head closes the open segment (the
-            // part before a chain's first head belongs to an earlier segment)
-            A accA = P::zero(), preA = P::zero(), accB = P::zero(), preB = P::zero();
-            int posA = -1, posB = -1;  // tile position of each chain's last head
-            const A initA = (lane == 0) ? cin : P::zero();  // lane 0's forced head takes the transmitter
-            // fast path: every chain of the warp holds at most one head, so a
-            // head only splits its chain into the part before it and after it
-            // (selects, no branches, no stores inside the loop)
-            const bool fast = __all_sync(FULL, cA <= 1 && cB <= 1);
-            auto fma_fast = [&](auto full_tag) {
-                constexpr bool FT = decltype(full_tag)::value;
-                const int hA = cA ? __ffs(hbA) - 1 : -1;
-                const int hB = cB ? __ffs(hbB) - 1 : -1;
+            // ---- per-lane sequential segmented sum, one FMA per entry in one
+            // chain (the FP64 pipe, not the chain's latency, sets the pace)
+            A acc = P::zero(), pre = P::zero();
+            int pos = -1;  // tile position of the lane's last head (EXACT)
+            if (!__any_sync(FULL, c > 1)) {
+                // at most one head per lane: it splits the run into the part
+                // before it (pre) and the segment it opens (acc); selects only
 #pragma unroll
-                for (int i = 0; i < HA; ++i) {
-                    const int kA = lane * W + i;
-                    const bool hdA = i == hA;
-                    preA = hdA ? accA : preA;
-                    accA = hdA ? initA : accA;
-                    if (FT || kA < len) accA = P::fma(vs[kA], xv[i], accA);
-                    if (i < HB) {
-                        const int kB = lane * W + HA + i;
-                        const bool hdB = i == hB;
-                        preB = hdB ? accB : preB;
-                        accB = hdB ? P::zero() : accB;
-                        if (FT || kB < len) accB = P::fma(vs[kB], xv[HA + i], accB);
-                    }
+                for (int i = 0; i < W; ++i) {
+                    const bool h = (hb >> i) & 1u;
+                    pre = h ? acc : pre;
+                    acc = h ? ((i == 0 && lane == 0) ? cin : P::zero()) : acc;
+                    acc = P::fma(vs[lane * W + i], xv[i], acc);
                 }
-                posA = cA ? lane * W + hA : -1;
-                posB = cB ? lane * W + HA + hB : -1;
-            };
-            // general path: any number of heads per chain
-            auto fma_general = [&](auto full_tag) {
-                constexpr bool FT = decltype(full_tag)::value;
-                int curA = idx0 - 1, curB = idx0 + cA - 1;
-#pragma unroll
-                for (int i = 0; i < HA; ++i) {
-                    const int kA = lane * W + i;
-                    if ((hbA >> i) & 1u) {
-                        if (curA >= idx0) emit(curA, accA, posA);
-                        else preA = accA;
-                        ++curA;
-                        posA = kA;
-                        accA = (i == 0) ? initA : P::zero();
-                    }
-                    if (FT || kA < len) accA = P::fma(vs[kA], xv[i], accA);
-                    if (i < HB) {
-                        const int kB = lane * W + HA + i;
-                        if ((hbB >> i) & 1u) {
-                            if (curB >= idx0 + cA) emit(curB, accB, posB);
-                            else preB = accB;
-                            ++curB;
-                            posB = kB;
-                            accB = P::zero();
-                        }
-                        if (FT || kB < len) accB = P::fma(vs[kB], xv[HA + i], accB);
-                    }
-                }
-            };
-            if (fast) {
-                if (full) fma_fast(std::true_type{});
-                else fma_fast(std::false_type{});
+                if (EXACT && c) pos = lane * W + __ffs(hb) - 1;
             } else {
-                if (full) fma_general(std::true_type{});
-                else fma_general(std::false_type{});
+                // general case: a head closes the open segment (the part
+                // before the lane's first head belongs to an earlier segment)
+                int cur = idx0 - 1;
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    if ((hb >> i) & 1u) {
+                        if (cur >= idx0) emit(cur, acc, pos);
+                        else pre = acc;
+                        ++cur;
+                        if (EXACT) pos = lane * W + i;
+                        acc = (i == 0 && lane == 0) ? cin : P::zero();
+                    }
+                    acc = P::fma(vs[lane * W + i], xv[i], acc);
+                }
             }
-            if (cA == 0) preA = accA;  // chain totals when a chain has no head
-            if (cB == 0) preB = accB;
-            // join the chains with one add: A's open part + B's leading part
-            const A join = P::add(accA, preB);
-            if (cA > 0 && cB > 0) emit(idx0 + cA - 1, join, posA);
-            const int lastpos = (cB > 0) ? posB : posA;  // the lane's last head
-            const A pre = (cA > 0) ? preA : join;  // the lane's part before its first head
-            const A v = (cB > 0) ? accB : join;    // suffix if the lane has a head, else total
+            if (c == 0) pre = acc;  // the lane's total when it has no head
+            const A v = acc;        // suffix if the lane has a head, else total
             const bool has = c > 0;
 
             // ---- cross-lane segmented sum of the open segments:
@@ -575,19 +574,20 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
                 }
             }
             const A Cprev = P::shfl_up(C, 1);
-            // head positions of the segments left open: the last head of the
-            // nearest earlier lane with one, and of lane `first` for lane 31
-            const unsigned below = hm & ((1u << lane) - 1u);
-            const int src = below ? 31 - __clz(below) : 0;
-            const int prevpos = __shfl_sync(FULL, lastpos, src);
-            const int openpos = __shfl_sync(FULL, lastpos, first);
+            int prevpos = -1, openpos = -1;
+            if (EXACT) {  // head positions of the segments left open
+                const int lastpos = pos;
+                const unsigned below = hm & ((1u << lane) - 1u);
+                prevpos = __shfl_sync(FULL, lastpos, below ? 31 - __clz(below) : 0);
+                openpos = __shfl_sync(FULL, lastpos, first);
+            }
             // a lane with a head closes the segment left open before it
             if (has && lane > 0) emit(idx0 - 1, P::add(Cprev, pre), prevpos);
             // the tile's last segment: stored, or carried if row `stop` goes on
             if (lane == 31) {
+                *slot_carry = C;
                 if (nseg == 1 && start == rF) {
-                    fval = C;  // still the bunch's first segment
-                    fhave = true;
+                    *slot_f = C;  // still the bunch's first segment
                 } else if (cont) {
                     if (t == t1 - 1) {  // continues into the next bunch
                         G = C;
@@ -600,11 +600,8 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
             if (lane == 0)
                 a.tile_info[t] = (uint32_t)nseg | (dirty ? kInfoDirty : 0u) |
                                  (resolve ? kInfoResolved : 0u);
-            carry = P::shfl(C, 31);
-            if (start == rF) {  // exactly one lane made segment 0 of this tile
-                const unsigned fm = __ballot_sync(FULL, fhave);
-                F = P::shfl(fval, fm ? __ffs(fm) - 1 : 0);
-            }
+            __syncwarp();
+            carry = *slot_carry;
             ++q_con;
             issue_next();  // the stage just consumed takes the next copy
             start = start_nx;
@@ -613,6 +610,8 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
             pr_chunk2 = pr_nx2;
         }
         // ---- synchronizer record of the bunch; its sums are finished in FP64
+        __syncwarp();
+        const A F = *slot_f;
         if (lane == 31) {
             a.sync_idx[cur] = rF;
             static_cast<double *>(a.sync_val)[cur] = P::to_f64(F);
@@ -622,7 +621,7 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
         claim_next();
         cur = nxt;
         nxt = -1;
-        if (cur >= a.nbunches) break;
+        if (cur >= nb) break;
     }
 }
 

@@ -38,7 +38,7 @@ class SsspmvError(RuntimeError):
 
 
 class ssspmv_opts(ctypes.Structure):
-    _fields_ = [("W", ctypes.c_int32), ("S", ctypes.c_int32), ("validate", ctypes.c_int32),
+    _fields_ = [("W", ctypes.c_int32), ("S", ctypes.c_int32), ("block_warps", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("timer", ctypes.c_void_p)]
 
 
@@ -124,9 +124,10 @@ def _stream(s):
 VARIANT_DEFAULT, VARIANT_SPECULATIVE, VARIANT_EXACT = 0, 1, 2
 
 
-def make_opts(W: int = 0, S: int = 0, timer=None, variant: int = 0) -> ssspmv_opts:
+def make_opts(W: int = 0, S: int = 0, timer=None, variant: int = 0,
+              block_warps: int = 0) -> ssspmv_opts:
     o = ssspmv_opts()
-    o.W, o.S, o.validate, o.variant = W, S, 0, variant
+    o.W, o.S, o.block_warps, o.variant = W, S, block_warps, variant
     o.timer = timer
     return o
 

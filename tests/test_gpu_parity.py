@@ -32,22 +32,23 @@ def _api():
     return api, ssspmv
 
 
-def check_case(dev, row_ptr, col, val, x, n, W=0, S=0, expect_exact=None, variant=None):
+def check_case(dev, row_ptr, col, val, x, n, W=0, S=0, expect_exact=None, variant=None,
+               block_warps=0):
     """Runs both dirty-tile variants (speculative + calibration, and exact
     stores in kernel (b)) unless one is given; returns the last result."""
     _, C = _api()
     variants = [C.VARIANT_SPECULATIVE, C.VARIANT_EXACT] if variant is None else [variant]
     out = None
     for v in variants:
-        out = _check_one(dev, row_ptr, col, val, x, n, W, S, expect_exact, v)
+        out = _check_one(dev, row_ptr, col, val, x, n, W, S, expect_exact, v, block_warps)
     return out
 
 
-def _check_one(dev, row_ptr, col, val, x, n, W, S, expect_exact, variant):
+def _check_one(dev, row_ptr, col, val, x, n, W, S, expect_exact, variant, block_warps=0):
     api, C = _api()
     A = api.to_device(row_ptr, col, val, n, dev)
     xd = torch.as_tensor(x, dtype=torch.float64, device=dev)
-    opts = C.make_opts(W=W, S=S, variant=variant)
+    opts = C.make_opts(W=W, S=S, variant=variant, block_warps=block_warps)
     out = api.spmv_f64_debug(A, xd, opts)
     shape = out["shape"]
     L = shape["L"]
@@ -95,6 +96,19 @@ def test_uniform4096_all_shapes(dev):
     for W in _api()[1].ssspmv_supported_w():
         for S in (0, 1, 2, 7):
             check_case(dev, A.row_ptr, A.col, A.val, x, A.n, W=W, S=S)
+
+
+@pytest.mark.parametrize("bw", [1, 3, 8, 17, 64])
+def test_block_warps(dev, bw):
+    """Kernel (b) launched with fewer warps per block than it was compiled
+    for, and with an over-large request (lowered to the most that fit), gives
+    the same rows and index artefacts."""
+    lens = synth.random_lengths(30000, seed=11, mean=6.0, p_empty=0.3, p_long=0.001,
+                                long_len=3000)
+    A = synth.from_lengths(lens, 5000, seed=11)
+    x = synth.sym_vector(A.n, seed=11)
+    for W in (0, 27):
+        check_case(dev, A.row_ptr, A.col, A.val, x, A.n, W=W, block_warps=bw)
 
 
 @pytest.mark.parametrize("seed,mean,p_empty,p_long,long_len", [
