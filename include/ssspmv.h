@@ -127,7 +127,10 @@ size_t ssspmv_workspace_bytes(int32_t m, int32_t nnz, int32_t val_bytes, const s
 
 /* y = A x in FP64 (val, x, y double).  workspace: device buffer of at least
  * ssspmv_workspace_bytes(m, nnz, 8, opts) bytes, 256-byte aligned, not used
- * by another call in flight.  Kernels: (a), (b), (c) above. */
+ * by another call in flight -- or NULL (ws_bytes ignored) for a buffer the
+ * library owns, cached per (device, stream) and grown stream-ordered with
+ * cudaMallocAsync on `stream` when a call needs more (see
+ * ssspmv_cached_workspace).  Kernels: (a), (b), (c) above. */
 int ssspmv_csr_f64(int32_t m, int32_t n, int32_t nnz,
                    const int32_t *row_ptr, const int32_t *col_idx, const double *val,
                    const double *x, double *y,
@@ -148,6 +151,42 @@ int ssspmv_csr_bf16f32(int32_t m, int32_t n, int32_t nnz,
                        const int32_t *row_ptr, const int32_t *col_idx, const uint16_t *val,
                        const float *x, float *y,
                        const ssspmv_opts *opts, void *workspace, size_t ws_bytes, void *stream);
+
+/* The library-owned workspace of the current device and `stream` (the one
+ * calls with workspace == NULL use), e.g. for ssspmv_device_status.  Returns
+ * SSSPMV_EWORKSPACE (and NULL, 0) if no call on that stream has made one yet.
+ * ssspmv_release_workspaces frees every cached buffer (cudaFree: waits for the
+ * work still using them); call it when no call is in flight. */
+int ssspmv_cached_workspace(void *stream, void **ptr, size_t *bytes);
+void ssspmv_release_workspaces(void);
+
+/* Partition reuse for iterative solvers (one sparsity pattern, many
+ * products).  The paper has no plan -- its method needs no preprocessing
+ * (Sec. 1), and the single calls above are what the headline numbers time --
+ * but kernel (a) depends on row_ptr alone, so a plan runs it once:
+ *   ssspmv_plan_create  checks the arguments, resolves the tile shape for the
+ *     stored value type (val_bytes 8, 4 or 2; opts as for the single calls,
+ *     opts->timer must be NULL), takes `workspace` (NULL: the plan allocates
+ *     one with cudaMalloc and owns it) and launches kernel (a) on `stream`.
+ *     row_ptr stays the caller's: it must remain valid and unchanged while
+ *     the plan lives (kernel (b) reads it on every execution).
+ *   ssspmv_plan_execute  y = A x with the plan's partition: kernels (b) and
+ *     (c) on `stream`, for col_idx/val/x/y of the plan's value type (double,
+ *     float, or bf16 val with float x and y).  It allocates nothing; `timer`
+ *     (nullable ssspmv_timer*) records it, its kernel (a) slot then timing the
+ *     reset of the error word.  Executions of one plan share its workspace:
+ *     order them on one stream.  Must run on the plan's device.
+ *   ssspmv_plan_workspace  the plan's workspace (for ssspmv_device_status).
+ *   ssspmv_plan_destroy  frees what the plan owns (cudaFree: waits for the
+ *     device). */
+typedef struct ssspmv_plan ssspmv_plan;
+int ssspmv_plan_create(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr,
+                       int32_t val_bytes, const ssspmv_opts *opts, void *workspace,
+                       size_t ws_bytes, void *stream, ssspmv_plan **out);
+int ssspmv_plan_execute(ssspmv_plan *plan, const int32_t *col_idx, const void *val,
+                        const void *x, void *y, void *timer, void *stream);
+int ssspmv_plan_workspace(const ssspmv_plan *plan, void **ptr, size_t *bytes);
+void ssspmv_plan_destroy(ssspmv_plan *plan);
 
 /* Allocation-free FP64 product.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- code handed

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <vector>
+#include <mutex>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -147,6 +149,58 @@ static int check_csr_args(int32_t m, int32_t n, int32_t nnz, const void *row_ptr
     return SSSPMV_OK;
 }
 
+// ---------------------------------------------------------------------------
+// library-owned workspaces, one per (device, stream), grown stream-ordered
+
+namespace {
+struct CachedWs {
+    int dev;
+    void *stream;
+    void *base;    // what cudaMallocAsync returned
+    void *ptr;     // 256-byte aligned start
+    size_t bytes;  // usable bytes from ptr
+};
+std::mutex g_ws_mutex;
+std::vector<CachedWs> g_ws;
+}  // namespace
+
+static int cached_workspace(size_t need, void *stream, void **ptr, size_t *bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return record_cuda_error(e);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lock(g_ws_mutex);
+    CachedWs *slot = nullptr;
+    for (auto &w : g_ws)
+        if (w.dev == dev && w.stream == stream) slot = &w;
+    if (slot && slot->bytes >= need) {
+        *ptr = slot->ptr;
+        *bytes = slot->bytes;
+        return SSSPMV_OK;
+    }
+    if (slot && slot->base) {
+        // calls already queued on this stream finish with the old buffer first
+        if ((e = cudaFreeAsync(slot->base, s)) != cudaSuccess) return record_cuda_error(e);
+        slot->base = slot->ptr = nullptr;
+        slot->bytes = 0;
+    }
+    const size_t want = need + need / 4 + 256;  // room to grow a little
+    void *base = nullptr;
+    if ((e = cudaMallocAsync(&base, want, s)) != cudaSuccess) return record_cuda_error(e);
+    if (!slot) {
+        g_ws.push_back(CachedWs{dev, stream, nullptr, nullptr, 0});
+        slot = &g_ws.back();
+    }
+    const uintptr_t a = ((uintptr_t)base + 255u) & ~(uintptr_t)255u;
+    slot->base = base;
+    slot->ptr = reinterpret_cast<void *>(a);
+    slot->bytes = want - (a - (uintptr_t)base);
+    *ptr = slot->ptr;
+    *bytes = slot->bytes;
+    return SSSPMV_OK;
+}
+
 static int run_call(int32_t val_bytes, int32_t m, int32_t n, int32_t nnz,
                     const int32_t *row_ptr, const int32_t *col, const void *val, const void *x,
                     void *y, const ssspmv_opts *opts, void *ws, size_t ws_bytes, void *stream,
@@ -161,7 +215,11 @@ static int run_call(int32_t val_bytes, int32_t m, int32_t n, int32_t nnz,
     if (rc) return rc;
     if (out_layout) *out_layout = l;
     if (m == 0) return SSSPMV_OK;
-    if (!ws || ws_bytes < l.total || ((uintptr_t)ws & 255u)) return SSSPMV_EWORKSPACE;
+    if (!ws) {
+        rc = cached_workspace(l.total, stream, &ws, &ws_bytes);
+        if (rc) return rc;
+    }
+    if (ws_bytes < l.total || ((uintptr_t)ws & 255u)) return SSSPMV_EWORKSPACE;
     rc = pr->resolve(l, opts ? opts->S : 0);
     if (rc) return rc;
     if (l.nbunches > l.nbunch_cap) return SSSPMV_EWORKSPACE;
@@ -349,12 +407,168 @@ int ssspmv_csr_bf16f32(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr
                     nullptr, nullptr, nullptr);
 }
 
+// ---------------------------------------------------------------------------
+// plans: kernel (a) once, kernels (b) and (c) per execution
+
+struct ssspmv_plan {
+    int32_t m = 0, n = 0, nnz = 0, val_bytes = 0;
+    const int32_t *row_ptr = nullptr;
+    Layout lay;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool owns_ws = false;
+    int exact = 0, block_warps = 0, dev = 0;
+};
+
+int ssspmv_plan_create(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr,
+                       int32_t val_bytes, const ssspmv_opts *opts, void *workspace,
+                       size_t ws_bytes, void *stream, ssspmv_plan **out)
+{
+    if (!out) return SSSPMV_EINVAL;
+    *out = nullptr;
+    const Prec *pr = prec_for(val_bytes);
+    if (!pr) return SSSPMV_EUNSUPPORTED;
+    if (m < 0 || n < 0 || nnz < 0 || (m == 0 && nnz != 0)) return SSSPMV_EINVAL;
+    if (m > 0 && !row_ptr) return SSSPMV_EINVAL;
+    if (opts && opts->timer) return SSSPMV_EINVAL;  // time executions, not the plan
+    Layout l;
+    int rc = make_layout(m, nnz, val_bytes, opts, l);
+    if (rc) return rc;
+    rc = pr->resolve(l, opts ? opts->S : 0);
+    if (rc) return rc;
+    ssspmv_plan *p = new (std::nothrow) ssspmv_plan;
+    if (!p) return SSSPMV_EINVAL;
+    p->m = m;
+    p->n = n;
+    p->nnz = nnz;
+    p->val_bytes = val_bytes;
+    p->row_ptr = row_ptr;
+    p->lay = l;
+    p->exact = (opts && opts->variant == SSSPMV_VARIANT_EXACT) ? 1 : 0;
+    p->block_warps = opts ? opts->block_warps : 0;
+    if (workspace && (ws_bytes < l.total || ((uintptr_t)workspace & 255u))) {
+        delete p;
+        return SSSPMV_EWORKSPACE;
+    }
+    cudaError_t e = cudaGetDevice(&p->dev);
+    if (e != cudaSuccess) {
+        delete p;
+        return record_cuda_error(e);
+    }
+    if (workspace) {
+        p->ws = workspace;
+        p->ws_bytes = ws_bytes;
+    } else if (l.total > 0) {
+        e = cudaMalloc(&p->ws, l.total);
+        if (e != cudaSuccess) {
+            delete p;
+            return record_cuda_error(e);
+        }
+        p->ws_bytes = l.total;
+        p->owns_ws = true;
+    }
+    if (m > 0) {
+        // kernel (a) alone: the tile offsets (and a cleared error word/ticket)
+        unsigned char *w = static_cast<unsigned char *>(p->ws);
+        launch_partition(row_ptr, m, nnz, l.L, l.ntiles,
+                         reinterpret_cast<int32_t *>(w + l.off_tile_offset),
+                         reinterpret_cast<uint32_t *>(w + l.off_err),
+                         static_cast<cudaStream_t>(stream), partition_method(m, l.ntiles));
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            ssspmv_plan_destroy(p);
+            return record_cuda_error(e);
+        }
+    }
+    *out = p;
+    return SSSPMV_OK;
+}
+
+int ssspmv_plan_execute(ssspmv_plan *p, const int32_t *col_idx, const void *val, const void *x,
+                        void *y, void *timer, void *stream)
+{
+    if (!p) return SSSPMV_EINVAL;
+    const Prec *pr = prec_for(p->val_bytes);
+    if (!pr) return SSSPMV_EUNSUPPORTED;
+    int rc = check_csr_args(p->m, p->n, p->nnz, p->row_ptr, col_idx, val, x, y);
+    if (rc) return rc;
+    if (p->m == 0) return SSSPMV_OK;
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return record_cuda_error(e);
+    if (dev != p->dev) return SSSPMV_EINVAL;  // a plan belongs to the device it was made on
+    Call c;
+    c.m = p->m;
+    c.n = p->n;
+    c.nnz = p->nnz;
+    c.row_ptr = p->row_ptr;
+    c.col = col_idx;
+    c.val = val;
+    c.x = x;
+    c.y = y;
+    c.lay = p->lay;
+    c.ws = static_cast<unsigned char *>(p->ws);
+    c.stream = static_cast<cudaStream_t>(stream);
+    c.ev = timer ? timer_next_slot(static_cast<ssspmv_timer *>(timer)) : nullptr;
+    c.exact = p->exact;
+    c.block_warps = p->block_warps;
+    c.skip_partition = 1;
+    return pr->run(c);
+}
+
+int ssspmv_plan_workspace(const ssspmv_plan *p, void **ptr, size_t *bytes)
+{
+    if (!p) return SSSPMV_EINVAL;
+    if (ptr) *ptr = p->ws;
+    if (bytes) *bytes = p->ws_bytes;
+    return SSSPMV_OK;
+}
+
+void ssspmv_plan_destroy(ssspmv_plan *p)
+{
+    if (!p) return;
+    if (p->owns_ws && p->ws) cudaFree(p->ws);
+    delete p;
+}
+
+int ssspmv_cached_workspace(void *stream, void **ptr, size_t *bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return record_cuda_error(e);
+    std::lock_guard<std::mutex> lock(g_ws_mutex);
+    for (auto &w : g_ws)
+        if (w.dev == dev && w.stream == stream && w.ptr) {
+            if (ptr) *ptr = w.ptr;
+            if (bytes) *bytes = w.bytes;
+            return SSSPMV_OK;
+        }
+    if (ptr) *ptr = nullptr;
+    if (bytes) *bytes = 0;
+    return SSSPMV_EWORKSPACE;
+}
+
+void ssspmv_release_workspaces(void)
+{
+    std::lock_guard<std::mutex> lock(g_ws_mutex);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &w : g_ws) {
+        if (!w.base) continue;
+        cudaSetDevice(w.dev);
+        cudaFree(w.base);  // waits for the work still using it
+    }
+    cudaSetDevice(cur);
+    g_ws.clear();
+}
+
 int ssspmv_csr_f64_debug(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr,
                          const int32_t *col_idx, const double *val, const double *x, double *y,
                          const ssspmv_opts *opts, void *workspace, size_t ws_bytes, void *stream,
                          int32_t *tile_offset, uint32_t *desc, uint32_t *tile_info,
                          int32_t *sync_idx, double *y_spec)
 {
+    if (!workspace) return SSSPMV_EWORKSPACE;  // the artefacts are read back from it
     Layout l;
     int rc = run_call(8, m, n, nnz, row_ptr, col_idx, val, x, y, opts, workspace, ws_bytes, stream,
                       desc, y_spec, &l);

@@ -20,6 +20,7 @@ struct Call {
     cudaEvent_t *ev = nullptr;       // 4 library-owned events or null
     int exact = 0;                   // dirty tiles store in their true rows
     int block_warps = 0;             // warps per block of kernel (b); 0: the most that fit
+    int skip_partition = 0;          // plan execution: tile offsets already in the workspace
     uint32_t *dbg_desc = nullptr;    // ntiles*W words or null
     void *dbg_yspec = nullptr;       // m values or null
 };
@@ -102,7 +103,12 @@ int run_shape(const Call &c)
 
     if (c.ev && (e = cudaEventRecord(c.ev[0], c.stream)) != cudaSuccess)
         return record_cuda_error(e);
-    {
+    if (c.skip_partition) {
+        // the partition is the plan's; only the error word and the bunch
+        // ticket (cleared by kernel (a) otherwise) start again from zero
+        if ((e = cudaMemsetAsync(err, 0, 2 * sizeof(uint32_t), c.stream)) != cudaSuccess)
+            return record_cuda_error(e);
+    } else {
         launch_partition(c.row_ptr, c.m, c.nnz, l.L, l.ntiles, toff, err, c.stream,
                          partition_method(c.m, l.ntiles));
     }

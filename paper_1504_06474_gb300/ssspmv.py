@@ -65,6 +65,12 @@ _SIGS = {
     "ssspmv_timer_destroy": (None, [P]),
     "ssspmv_timer_reset": (None, [P]),
     "ssspmv_timer_read": (ctypes.c_int, [P, P, i32, P]),
+    "ssspmv_cached_workspace": (ctypes.c_int, [P, P, P]),
+    "ssspmv_release_workspaces": (None, []),
+    "ssspmv_plan_create": (ctypes.c_int, [i32, i32, i32, P, i32, OPTS, P, sz, P, P]),
+    "ssspmv_plan_execute": (ctypes.c_int, [P, P, P, P, P, P, P]),
+    "ssspmv_plan_workspace": (ctypes.c_int, [P, P, P]),
+    "ssspmv_plan_destroy": (None, [P]),
     "ssspmv_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "ssspmv_last_cuda_error": (ctypes.c_int, []),
     "ssspmv_version": (ctypes.c_int, []),
@@ -259,6 +265,46 @@ def ssspmv_timer_read(timer: int, cap: int):
     check(_lib().ssspmv_timer_read(timer, buf, cap, ctypes.byref(cnt)), "ssspmv_timer_read")
     n = min(cnt.value, cap)
     return [tuple(buf[4 * i + j] for j in range(4)) for i in range(n)]
+
+
+def ssspmv_cached_workspace(stream=None):
+    """(pointer, bytes) of the library-owned workspace of this device and stream."""
+    p, b = ctypes.c_void_p(), ctypes.c_size_t()
+    rc = _lib().ssspmv_cached_workspace(_stream(stream), ctypes.byref(p), ctypes.byref(b))
+    check(rc, "ssspmv_cached_workspace")
+    return p.value, b.value
+
+
+def ssspmv_release_workspaces() -> None:
+    _lib().ssspmv_release_workspaces()
+
+
+def ssspmv_plan_create(m, n, nnz, row_ptr, val_bytes=8, opts=None, workspace=None,
+                       ws_bytes=None, stream=None) -> int:
+    """Returns the plan handle (an int); raises SsspmvError on failure."""
+    if ws_bytes is None:
+        ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    h = ctypes.c_void_p()
+    rc = _lib().ssspmv_plan_create(m, n, nnz, _ptr(row_ptr), val_bytes, _opts(opts),
+                                   _ptr(workspace), ws_bytes, _stream(stream), ctypes.byref(h))
+    check(rc, "ssspmv_plan_create")
+    return h.value
+
+
+def ssspmv_plan_execute(plan, col_idx, val, x, y, timer=None, stream=None) -> int:
+    return _lib().ssspmv_plan_execute(plan, _ptr(col_idx), _ptr(val), _ptr(x), _ptr(y), timer,
+                                      _stream(stream))
+
+
+def ssspmv_plan_workspace(plan):
+    p, b = ctypes.c_void_p(), ctypes.c_size_t()
+    check(_lib().ssspmv_plan_workspace(plan, ctypes.byref(p), ctypes.byref(b)),
+          "ssspmv_plan_workspace")
+    return p.value, b.value
+
+
+def ssspmv_plan_destroy(plan) -> None:
+    _lib().ssspmv_plan_destroy(plan)
 
 
 def ssspmv_strerror(code: int) -> str:

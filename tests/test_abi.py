@@ -73,8 +73,14 @@ def test_null_and_misaligned(lib):
 
 def test_workspace_checks(lib):
     need = S.ssspmv_workspace_bytes(100, 1000, 8, None)
+    # workspace=None asks for the library-owned buffer; with no GPU here the
+    # device lookup fails before anything is allocated or launched
     rc = S.ssspmv_csr_f64(100, 100, 1000, FAKE, FAKE, FAKE, FAKE, FAKE, workspace=None,
                           ws_bytes=need)
+    assert rc == S.SSSPMV_ECUDA
+    # the debug entry point reads its artefacts back from the workspace: it needs one
+    rc = S._lib().ssspmv_csr_f64_debug(100, 100, 1000, FAKE, FAKE, FAKE, FAKE, FAKE, None, None,
+                                       0, None, None, None, None, None, None)
     assert rc == S.SSSPMV_EWORKSPACE
     rc = S.ssspmv_csr_f64(100, 100, 1000, FAKE, FAKE, FAKE, FAKE, FAKE, workspace=FAKE,
                           ws_bytes=need - 1)
@@ -110,3 +116,28 @@ def test_torch_layer_imports(lib):
     from paper_1504_06474_gb300 import api, ssspmv
     assert callable(api.spmv_f64) and callable(api.spmv_f64_debug)
     assert api._c is ssspmv
+
+
+def test_plan_host_checks(lib):
+    import ctypes
+    h = ctypes.c_void_p()
+    L = S._lib()
+    # bad scalars, missing row_ptr, unknown value type, no output handle
+    assert L.ssspmv_plan_create(-1, 4, 0, FAKE, 8, None, None, 0, None, ctypes.byref(h)) == S.SSSPMV_EINVAL
+    assert L.ssspmv_plan_create(0, 4, 3, FAKE, 8, None, None, 0, None, ctypes.byref(h)) == S.SSSPMV_EINVAL
+    assert L.ssspmv_plan_create(4, 4, 8, None, 8, None, None, 0, None, ctypes.byref(h)) == S.SSSPMV_EINVAL
+    assert L.ssspmv_plan_create(4, 4, 8, FAKE, 3, None, None, 0, None, ctypes.byref(h)) == S.SSSPMV_EUNSUPPORTED
+    assert L.ssspmv_plan_create(4, 4, 8, FAKE, 8, None, None, 0, None, None) == S.SSSPMV_EINVAL
+    # a timer belongs to executions, not to the plan
+    o = S.make_opts(timer=12345)
+    assert L.ssspmv_plan_create(4, 4, 8, FAKE, 8, ctypes.byref(o), None, 0, None,
+                                ctypes.byref(h)) == S.SSSPMV_EINVAL
+    # a caller workspace that is too small or misaligned is refused before any launch
+    need = S.ssspmv_workspace_bytes(100, 1000, 8, None)
+    assert L.ssspmv_plan_create(100, 100, 1000, FAKE, 8, None, FAKE, need - 1, None,
+                                ctypes.byref(h)) == S.SSSPMV_EWORKSPACE
+    assert L.ssspmv_plan_create(100, 100, 1000, FAKE, 8, None, FAKE + 16, need, None,
+                                ctypes.byref(h)) == S.SSSPMV_EWORKSPACE
+    assert h.value is None
+    assert L.ssspmv_plan_execute(None, FAKE, FAKE, FAKE, FAKE, None, None) == S.SSSPMV_EINVAL
+    S.ssspmv_plan_destroy(None)  # a no-op
