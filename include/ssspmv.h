@@ -66,6 +66,9 @@ extern "C" {
 #define SSSPMV_DEV_TIMEOUT   1u  /* a bounded wait on a bulk copy gave up */
 #define SSSPMV_DEV_RANGE     2u  /* a computed row index fell outside [0, m) */
 #define SSSPMV_DEV_CALIB     4u  /* calibration found a segment count that does not match row_ptr */
+#define SSSPMV_DEV_BATCH     8u  /* a batch descriptor was invalid (that matrix was skipped) or
+                                    the batch exceeded the capacity its workspace was sized for
+                                    (nothing was computed) */
 
 /* Storing the partial sums of tiles that hold empty rows ("dirty" tiles):
  *  SPECULATIVE  the paper's method: kernel (b) stores every segment at its
@@ -187,6 +190,41 @@ int ssspmv_plan_execute(ssspmv_plan *plan, const int32_t *col_idx, const void *v
                         const void *x, void *y, void *timer, void *stream);
 int ssspmv_plan_workspace(const ssspmv_plan *plan, void **ptr, size_t *bytes);
 void ssspmv_plan_destroy(ssspmv_plan *plan);
+
+/* Batched FP32 products y_i = A_i x_i for `count` matrices of any sizes in
+ * one pass: a set-up kernel, kernel (a) over every matrix, ONE persistent
+ * launch of kernel (b) over every bunch of every matrix (bunches never cross
+ * matrices) and kernel (c) over all of them -- four launches whatever the
+ * count, no host synchronisation and no allocation, so the call can be
+ * captured in a CUDA graph.  The paper runs one matrix at a time; batching is
+ * this library's addition.
+ *   mats       DEVICE array of `count` descriptors, 8-byte aligned; each
+ *              describes one matrix exactly as the single FP32 call takes it
+ *              (float val, x, y; col_idx and val 16-byte aligned; reserved 0).
+ *              An invalid descriptor is skipped (its y untouched) and sets
+ *              SSSPMV_DEV_BATCH in the workspace's error word.
+ *   total_nnz  an upper bound of the sum of the matrices' nnz: it sizes the
+ *              workspace (ssspmv_batched_workspace_bytes with the same count,
+ *              total_nnz and opts).  A batch that turns out larger computes
+ *              nothing and sets SSSPMV_DEV_BATCH.
+ *   opts       as for the single calls (one tile shape W and bunch size S for
+ *              the whole batch; opts->timer records the four launches as
+ *              set-up+(a), (b), (c)).
+ * Results equal the single FP32 call's bit for bit for every matrix. */
+typedef struct ssspmv_csr_desc {
+    int32_t m, n, nnz;
+    int32_t reserved;            /* must be 0 */
+    const int32_t *row_ptr;      /* [m+1] */
+    const int32_t *col_idx;      /* [nnz] */
+    const void *val;             /* [nnz] float */
+    const void *x;               /* [n] float */
+    void *y;                     /* [m] float, written */
+} ssspmv_csr_desc;               /* 56 bytes */
+size_t ssspmv_batched_workspace_bytes(int32_t count, int64_t total_nnz, int32_t val_bytes,
+                                      const ssspmv_opts *opts);
+int ssspmv_csr_batched_f32(int32_t count, const ssspmv_csr_desc *mats, int64_t total_nnz,
+                           const ssspmv_opts *opts, void *workspace, size_t ws_bytes,
+                           void *stream);
 
 /* Allocation-free FP64 product.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- code handed

@@ -14,7 +14,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libssspmv.so")
 
-SOURCES = ["api.cu", "partition.cu", "spmv_f64.cu", "spmv_f32.cu", "spmv_bf16.cu",
+SOURCES = ["api.cu", "partition.cu", "spmv_f64.cu", "spmv_f32.cu", "spmv_bf16.cu", "batched.cu",
            "noalloc.cu"]
 HEADERS = ["ptx.cuh", "segsum.cuh", "launch.cuh", "layout.h"]
 

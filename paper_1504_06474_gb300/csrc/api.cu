@@ -262,6 +262,9 @@ __global__ void validate_kernel(int32_t m, int32_t n, int32_t nnz, const int32_t
     }
 }
 
+int f32_run_batched(int32_t count, const void *desc, const BatchLayout &l, unsigned char *ws,
+                    cudaStream_t stream, int exact, int block_warps, cudaEvent_t *ev);  // batched.cu
+
 }  // namespace ssspmv
 
 using namespace ssspmv;
@@ -405,6 +408,54 @@ int ssspmv_csr_bf16f32(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr
 {
     return run_call(2, m, n, nnz, row_ptr, col_idx, val, x, y, opts, workspace, ws_bytes, stream,
                     nullptr, nullptr, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// batches
+
+static int make_batch_layout(int32_t count, int64_t total_nnz, int32_t val_bytes,
+                             const ssspmv_opts *o, BatchLayout &l)
+{
+    if (count < 0 || total_nnz < 0) return SSSPMV_EINVAL;
+    if (o && (o->S < 0 || o->block_warps < 0 || o->variant < 0 || o->variant > 2))
+        return SSSPMV_EINVAL;
+    int32_t W = 0;
+    int rc = resolve_w(0, 0, val_bytes, o, &W);
+    if (rc) return rc;
+    const int32_t S = (o && o->S > 0) ? o->S : kDefaultS;
+    // global tile and bunch numbers are 32-bit in the kernels
+    if (total_nnz / (32 * W) + count > (int64_t)SSSPMV_MAX_DIM) return SSSPMV_EINVAL;
+    batch_layout(count, total_nnz, W, S, l);
+    return SSSPMV_OK;
+}
+
+size_t ssspmv_batched_workspace_bytes(int32_t count, int64_t total_nnz, int32_t val_bytes,
+                                      const ssspmv_opts *opts)
+{
+    if (val_bytes != 4) return 0;
+    BatchLayout l;
+    if (make_batch_layout(count, total_nnz, val_bytes, opts, l)) return 0;
+    return l.total;
+}
+
+int ssspmv_csr_batched_f32(int32_t count, const ssspmv_csr_desc *mats, int64_t total_nnz,
+                           const ssspmv_opts *opts, void *workspace, size_t ws_bytes,
+                           void *stream)
+{
+    BatchLayout l;
+    int rc = make_batch_layout(count, total_nnz, 4, opts, l);
+    if (rc) return rc;
+    if (count == 0) return SSSPMV_OK;
+    if (!mats || ((uintptr_t)mats & 7u)) return SSSPMV_EINVAL;
+    if (!workspace || ws_bytes < l.total || ((uintptr_t)workspace & 255u))
+        return SSSPMV_EWORKSPACE;
+    cudaEvent_t *ev = (opts && opts->timer)
+                          ? timer_next_slot(static_cast<ssspmv_timer *>(opts->timer))
+                          : nullptr;
+    return f32_run_batched(count, mats, l, static_cast<unsigned char *>(workspace),
+                           static_cast<cudaStream_t>(stream),
+                           (opts && opts->variant == SSSPMV_VARIANT_EXACT) ? 1 : 0,
+                           opts ? opts->block_warps : 0, ev);
 }
 
 // ---------------------------------------------------------------------------

@@ -44,4 +44,44 @@ inline void carve(Layout &l)
     l.total = o;
 }
 
+// workspace carve-up of a batch (one 64-byte record per matrix, BatchMat)
+constexpr size_t kBatchMatBytes = 64;
+
+struct BatchLayout {
+    int32_t W = 0, L = 0, S = 0;
+    int64_t cap_tiles = 0, cap_bunches = 0;
+    size_t off_err = 0, off_mats = 0, off_toff = 0, off_info = 0, off_bmat = 0, off_sidx = 0,
+           off_sval = 0, off_tval = 0, off_tflag = 0, total = 0;
+};
+
+inline void batch_layout(int32_t count, int64_t total_nnz, int32_t W, int32_t S, BatchLayout &l)
+{
+    l.W = W;
+    l.L = 32 * W;
+    l.S = S;
+    l.cap_tiles = (total_nnz + l.L - 1) / l.L + count;
+    l.cap_bunches = (l.cap_tiles + S - 1) / S + count;
+    size_t o = 0;
+    l.off_err = o;  // err word, ticket, totals {tiles, bunches}
+    o = align256(o + 16);
+    l.off_mats = o;
+    o = align256(o + kBatchMatBytes * (size_t)(count > 0 ? count : 1));
+    l.off_toff = o;
+    o = align256(o + sizeof(int32_t) * (size_t)(l.cap_tiles + count));
+    l.off_info = o;
+    o = align256(o + sizeof(uint32_t) * (size_t)(l.cap_tiles > 0 ? l.cap_tiles : 1));
+    const size_t nb = (size_t)(l.cap_bunches > 0 ? l.cap_bunches : 1);
+    l.off_bmat = o;
+    o = align256(o + sizeof(int32_t) * nb);
+    l.off_sidx = o;
+    o = align256(o + sizeof(int32_t) * nb);
+    l.off_sval = o;
+    o = align256(o + sizeof(double) * nb);
+    l.off_tval = o;
+    o = align256(o + sizeof(double) * nb);
+    l.off_tflag = o;
+    o = align256(o + sizeof(int32_t) * nb);
+    l.total = o;
+}
+
 }  // namespace ssspmv

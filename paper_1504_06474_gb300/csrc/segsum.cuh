@@ -169,6 +169,29 @@ constexpr BlockShape pick_block_shape(int warp_bytes, int max_warps)
     return best;
 }
 
+// One matrix of a batch as the kernels see it: the caller's arrays plus its
+// place in the batch's global tile, bunch and row numbering (filled on the
+// device from the caller's descriptors by the batch set-up kernel).
+struct BatchMat {
+    const void *val;
+    const int32_t *col;
+    const int32_t *row_ptr;
+    const void *x;
+    void *y;
+    int32_t m, nnz;
+    int32_t tile_base;   // global index of its first tile
+    int32_t bunch_base;  // global index of its first bunch
+    int32_t ntiles;      // its tile count
+    int32_t row_base;    // global index of its first row
+};
+static_assert(sizeof(BatchMat) == kBatchMatBytes, "BatchMat is one 64-byte record");
+
+template <class T>
+__device__ __forceinline__ T *ldg_ptr(T *const *p)
+{
+    return reinterpret_cast<T *>(__ldg(reinterpret_cast<const unsigned long long *>(p)));
+}
+
 struct SegsumArgs {
     const int32_t *row_ptr;
     const int32_t *col;
@@ -189,6 +212,11 @@ struct SegsumArgs {
     int64_t ntiles;
     int64_t nbunches;
     int32_t S;
+    // batches only: the matrices, the matrix of every global bunch, and the
+    // batch totals {tiles, bunches} (all written on the device)
+    const BatchMat *mats = nullptr;
+    const int32_t *bunch_mat = nullptr;
+    const int32_t *totals = nullptr;
 };
 
 // tile_info layout: bit 31 dirty, bit 30 dirty and resolved by kernel (b),
@@ -255,7 +283,7 @@ __device__ __noinline__ uint32_t scan_rows_long(const int32_t *__restrict__ row_
 // order), then takes the remaining bunches one at a time from a ticket
 // counter, which evens out bunches that cost more (tiles over many rows).
 
-template <class P, int W, int B, int MINB, bool EXACT>
+template <class P, int W, int B, int MINB, bool EXACT, bool BATCHED = false>
 __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a)
 {
     using V = typename P::val_t;
@@ -278,8 +306,10 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
 
     // tiles, bunches, rows and positions all fit in 32 bits (the host
     // rejects m or nnz within 256 of the int32 limit)
-    const int32_t nb = (int32_t)a.nbunches;
-    const int32_t ntiles = (int32_t)a.ntiles;
+    // a batch is one global sequence of tiles and bunches; its totals are
+    // known on the device only
+    const int32_t nb = BATCHED ? __ldg(a.totals + 1) : (int32_t)a.nbunches;
+    const int32_t ntiles = BATCHED ? __ldg(a.totals) : (int32_t)a.ntiles;
     // blocks may be launched with fewer than B warps (more L1 per warp)
     const int32_t bw = (int32_t)(blockDim.x >> 5);
     const int32_t nwarps = (int32_t)gridDim.x * bw;
@@ -293,19 +323,55 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
     const int32_t dyn_base = nwarps * Q;
     int32_t cur = g * Q;
 
+    // the matrix of the current bunch (in a batch: reloaded per bunch);
+    // tbase is the global index of its first tile, shift its index in the
+    // batch (its tile offsets start at global position tbase + shift)
     const V *__restrict__ val = static_cast<const V *>(a.val);
     const X *__restrict__ x = static_cast<const X *>(a.x);
     Y *__restrict__ y = static_cast<Y *>(a.y);
     const int32_t *__restrict__ row_ptr = a.row_ptr;
     const int32_t *__restrict__ col = a.col;
-    const int32_t nnz = a.nnz;
+    int32_t nnz = a.nnz, mrows = a.m, tbase = 0, shift = 0;
     const int32_t S = a.S;
+    auto load_matrix = [&](int32_t mi) {
+        if constexpr (BATCHED) {
+            const BatchMat *mm = a.mats + mi;
+            val = static_cast<const V *>(ldg_ptr(&mm->val));
+            x = static_cast<const X *>(ldg_ptr(&mm->x));
+            y = static_cast<Y *>(ldg_ptr(const_cast<void *const *>(&mm->y)));
+            row_ptr = ldg_ptr(&mm->row_ptr);
+            col = ldg_ptr(&mm->col);
+            nnz = __ldg(&mm->nnz);
+            mrows = __ldg(&mm->m);
+            tbase = __ldg(&mm->tile_base);
+            shift = mi;
+        }
+    };
+    auto mat_of = [&](int32_t bb) -> int32_t {
+        if constexpr (BATCHED) return __ldg(a.bunch_mat + bb);
+        else return 0;
+    };
+    // global index of bunch bb's first tile, and one past its last
+    auto first_tile = [&](int32_t bb, int32_t mi) -> int32_t {
+        if constexpr (BATCHED)
+            return __ldg(&a.mats[mi].tile_base) + (bb - __ldg(&a.mats[mi].bunch_base)) * S;
+        else return bb * S;
+    };
 
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
 
-    auto bunch_end = [&](int32_t bb) { return (bb * S + S < ntiles) ? bb * S + S : ntiles; };
+    auto bunch_end = [&](int32_t bb, int32_t mi) -> int32_t {
+        if constexpr (BATCHED) {
+            const int32_t f = first_tile(bb, mi);
+            const int32_t e = __ldg(&a.mats[mi].tile_base) + __ldg(&a.mats[mi].ntiles);
+            return f + S < e ? f + S : e;
+        } else {
+            return (bb * S + S < ntiles) ? bb * S + S : ntiles;
+        }
+    };
     int32_t nxt = -1;  // the warp's next bunch, once known (warp-uniform)
+    int32_t ni = 0;    // its matrix
     uint32_t tk = 0;   // lane 0: a ticket requested ahead of its use
     bool tk_pending = false;
     auto request_ticket = [&]() {  // the atomic's round trip overlaps the bunch
@@ -317,40 +383,55 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
         if (nxt >= 0) return;
         if (cur + 1 < static_end) {
             nxt = cur + 1;
+            if (BATCHED && nxt < nb) ni = mat_of(nxt);
             return;
         }
         request_ticket();
         tk_pending = false;
         nxt = dyn_base + (int32_t)__shfl_sync(FULL, tk, 0);
+        if (BATCHED && nxt < nb) ni = mat_of(nxt);
     };
 
     auto stage_ptr = [&](uint32_t s) { return base + s * SM::STAGE_BYTES; };
-    // bulk copies of tile tt into stage s (lane 0 only)
-    auto issue = [&](int32_t tt, uint32_t s) {
-        const int32_t b = tt * L;
-        const int32_t len = (nnz - b < L) ? nnz - b : L;
+    // bulk copies of tile tt (of matrix mi) into stage s (lane 0 only)
+    auto issue = [&](int32_t tt, uint32_t s, int32_t mi) {
+        const V *vsrc = val;
+        const int32_t *csrc = col;
+        int32_t nz = nnz, tb = 0;
+        if constexpr (BATCHED) {
+            const BatchMat *mm = a.mats + mi;
+            vsrc = static_cast<const V *>(ldg_ptr(&mm->val));
+            csrc = ldg_ptr(&mm->col);
+            nz = __ldg(&mm->nnz);
+            tb = __ldg(&mm->tile_base);
+        }
+        const int32_t b = (tt - tb) * L;
+        const int32_t len = (nz - b < L) ? nz - b : L;
         const uint32_t vb = ((uint32_t)len * (uint32_t)sizeof(V)) & ~15u;
         const uint32_t cb = ((uint32_t)len * 4u) & ~15u;
         mbar_arrive_expect_tx(&bar[s], vb + cb);
-        if (vb) bulk_g2s(stage_ptr(s), val + b, vb, &bar[s], pol_stream);
-        if (cb) bulk_g2s(stage_ptr(s) + SM::VAL_REGION, col + b, cb, &bar[s], pol_stream);
+        if (vb) bulk_g2s(stage_ptr(s), vsrc + b, vb, &bar[s], pol_stream);
+        if (cb) bulk_g2s(stage_ptr(s) + SM::VAL_REGION, csrc + b, cb, &bar[s], pol_stream);
     };
     // the copy stream runs at most STAGES tiles ahead, into at most the next
     // bunch (warp-uniform: every lane calls it)
-    int32_t iss_b = cur, iss_t = cur * S;
+    int32_t ci = mat_of(cur);  // the current bunch's matrix
+    load_matrix(ci);
+    int32_t iss_b = cur, iss_i = ci, iss_t = first_tile(cur, ci);
     uint32_t q_iss = 0, q_con = 0;  // tiles issued / consumed by this warp
     auto issue_next = [&]() {
         if (iss_b >= nb) return;
-        if (iss_t >= bunch_end(iss_b)) {
+        if (iss_t >= bunch_end(iss_b, iss_i)) {
             if (iss_b != cur) return;
             claim_next();
             iss_b = nxt;
-            iss_t = nxt * S;
+            iss_i = ni;
             if (iss_b >= nb) return;
+            iss_t = first_tile(nxt, ni);
         }
         if (lane == 0) {
             fence_proxy_async_smem();
-            issue(iss_t, q_iss % STAGES);
+            issue(iss_t, q_iss % STAGES, iss_i);
         }
         ++q_iss;
         ++iss_t;
@@ -365,15 +446,15 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
 
     // boundary rows and the first row-pointer chunk of the next tile, loaded
     // one tile ahead (rows past m read row_ptr[m])
-    int32_t start = __ldg(a.tile_offset + cur * S);
-    int32_t stop = __ldg(a.tile_offset + cur * S + 1);
-    auto rp_at = [&](int32_t r) { return __ldg(row_ptr + (r < a.m ? r : a.m)); };
+    int32_t start = __ldg(a.tile_offset + first_tile(cur, ci) + shift);
+    int32_t stop = __ldg(a.tile_offset + first_tile(cur, ci) + shift + 1);
+    auto rp_at = [&](int32_t r) { return __ldg(row_ptr + (r < mrows ? r : mrows)); };
     int32_t pr_chunk = rp_at(start + lane);
     int32_t pr_chunk2 = rp_at(start + 32 + lane);
 
     while (true) {
         request_ticket();
-        const int32_t t0 = cur * S, t1 = bunch_end(cur);
+        const int32_t t0 = first_tile(cur, ci), t1 = bunch_end(cur, ci);
         const int32_t rF = start;  // the bunch's first row
         A carry = P::zero();
         A G = P::zero();
@@ -382,28 +463,33 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
         for (int32_t t = t0; t < t1; ++t) {
             const uint32_t s = q_con % STAGES;
             const uint32_t par = (q_con / STAGES) & 1u;
-            const int32_t b = t * L;
+            const int32_t b = (t - tbase) * L;  // the tile's entries [b, e) of its matrix
             const int32_t len = (nnz - b < L) ? nnz - b : L;
             const int32_t e = b + len;
 
             // ---- prefetch the next tile's rows (the next bunch's first tile
             // after the last one)
             int32_t start_nx = stop, stop_nx = 0, pr_nx = 0, pr_nx2 = 0;
-            bool have_nx = true;
             if (t + 1 < t1) {
-                stop_nx = __ldg(a.tile_offset + t + 2);
+                stop_nx = __ldg(a.tile_offset + t + 2 + shift);
+                pr_nx = rp_at(start_nx + lane);
+                pr_nx2 = rp_at(start_nx + 32 + lane);
             } else {
                 claim_next();
                 if (nxt < nb) {
-                    start_nx = __ldg(a.tile_offset + nxt * S);
-                    stop_nx = __ldg(a.tile_offset + nxt * S + 1);
-                } else {
-                    have_nx = false;
+                    const int32_t ft = first_tile(nxt, ni) + (BATCHED ? ni : 0);
+                    start_nx = __ldg(a.tile_offset + ft);
+                    stop_nx = __ldg(a.tile_offset + ft + 1);
+                    const int32_t *rp = row_ptr;
+                    int32_t mm = mrows;
+                    if constexpr (BATCHED) {
+                        rp = ldg_ptr(&a.mats[ni].row_ptr);
+                        mm = __ldg(&a.mats[ni].m);
+                    }
+                    const int32_t r1 = start_nx + lane, r2 = start_nx + 32 + lane;
+                    pr_nx = __ldg(rp + (r1 < mm ? r1 : mm));
+                    pr_nx2 = __ldg(rp + (r2 < mm ? r2 : mm));
                 }
-            }
-            if (have_nx) {
-                pr_nx = rp_at(start_nx + lane);
-                pr_nx2 = rp_at(start_nx + 32 + lane);
             }
 
             // ---- wait for this tile's val/col
@@ -477,8 +563,8 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
                 if (lane == 31 && start + 63 < stop) nx = rp_at(start + 64);
                 scan_row(start + 32 + lane, pr_chunk2, nx);
                 if (start + 64 <= stop) {  // long row ranges
-                    const uint32_t f = scan_rows_long<EXACT, Y>(row_ptr, a.m, start + 64, stop, b,
-                                                                len, desc, rowmap, y);
+                    const uint32_t f = scan_rows_long<EXACT, Y>(row_ptr, mrows, start + 64, stop,
+                                                                b, len, desc, rowmap, y);
                     dirty |= (f & 1u) != 0;
                     cont |= (f & 2u) != 0;
                 }
@@ -512,7 +598,7 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
                 } else {
                     int32_t row = start + sidx;
                     if (EXACT && resolve) row = hpos <= 0 ? start : rowmap[hpos < L ? hpos : 0];
-                    if (row >= 0 && row < a.m) y[row] = P::out(v);
+                    if (row >= 0 && row < mrows) y[row] = P::out(v);
                     else atomicOr(a.err, SSSPMV_DEV_RANGE);
                 }
             };
@@ -622,6 +708,12 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
         cur = nxt;
         nxt = -1;
         if (cur >= nb) break;
+        if constexpr (BATCHED) {
+            if (ni != ci) {
+                ci = ni;
+                load_matrix(ci);
+            }
+        }
     }
 }
 
@@ -649,6 +741,11 @@ struct CalibArgs {
     int32_t nblk_tiles;
     int32_t nblk_sync;
     int32_t nblk_zero;
+    // batches only (see SegsumArgs)
+    const BatchMat *mats = nullptr;
+    const int32_t *bunch_mat = nullptr;
+    const int32_t *totals = nullptr;
+    int32_t count = 0;
 };
 
 constexpr int kCalibWarps = 8;
@@ -658,18 +755,20 @@ constexpr int kCalibWarps = 8;
 // the s-th non-empty row inside (start, stop), and the empty rows there become
 // 0.  Rows are walked downwards so that every slot is read before any write
 // can reach it (a partial only moves up).
+// t is the tile's index in its matrix and tile_offset that matrix's offsets.
 template <class P>
-__device__ __forceinline__ void repair_dirty_tile(const CalibArgs &a, int64_t t, uint32_t info,
-                                                  int lane)
+__device__ __forceinline__ void repair_dirty_tile(const int32_t *__restrict__ row_ptr,
+                                                  typename P::y_t *__restrict__ y,
+                                                  const int32_t *__restrict__ tile_offset,
+                                                  int32_t m, int32_t nnz, int32_t L, int64_t t,
+                                                  uint32_t info, uint32_t *err, int lane)
 {
     using Y = typename P::y_t;
-    Y *__restrict__ y = static_cast<Y *>(a.y);
-    const int32_t *__restrict__ row_ptr = a.row_ptr;
     const int32_t nseg = (int32_t)(info & kInfoSegMask);
-    const int32_t start = __ldg(a.tile_offset + t);
-    const int32_t stop = __ldg(a.tile_offset + t + 1);
-    const int64_t e = (t + 1) * (int64_t)a.L < a.nnz ? (t + 1) * (int64_t)a.L : a.nnz;
-    const bool cont = stop < a.m && (int64_t)__ldg(row_ptr + stop) < e;
+    const int32_t start = __ldg(tile_offset + t);
+    const int32_t stop = __ldg(tile_offset + t + 1);
+    const int64_t e = (t + 1) * (int64_t)L < nnz ? (t + 1) * (int64_t)L : nnz;
+    const bool cont = stop < m && (int64_t)__ldg(row_ptr + stop) < e;
     // non-empty rows strictly inside (start, stop): each holds one segment
     const int32_t K = nseg - 1 - (cont ? 1 : 0);
     int32_t above = 0;
@@ -683,17 +782,31 @@ __device__ __forceinline__ void repair_dirty_tile(const CalibArgs &a, int64_t t,
         if (ne) {
             const int32_t sidx = K - q;
             if (sidx >= 1 && sidx <= K) v = y[start + sidx];
-            else atomicOr(a.err, SSSPMV_DEV_CALIB);
+            else atomicOr(err, SSSPMV_DEV_CALIB);
         }
         __syncwarp();
         if (valid) y[r] = ne ? v : Y(0);
         above += __popc(mask);
         __syncwarp();
     }
-    if (lane == 0 && above != K) atomicOr(a.err, SSSPMV_DEV_CALIB);
+    if (lane == 0 && above != K) atomicOr(err, SSSPMV_DEV_CALIB);
 }
 
-template <class P>
+// the batch matrix holding global tile t: the last one whose first tile is
+// at or before t (matrices without tiles share the next one's base)
+__device__ __forceinline__ int32_t batch_matrix_of_tile(const BatchMat *mats, int32_t count,
+                                                        int64_t t)
+{
+    int32_t lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo + 1) >> 1);
+        if ((int64_t)__ldg(&mats[mid].tile_base) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <class P, bool BATCHED = false>
 __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const CalibArgs a)
 {
     using Y = typename P::y_t;
@@ -701,15 +814,29 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     Y *__restrict__ y = static_cast<Y *>(a.y);
+    const int64_t ntiles = BATCHED ? (int64_t)__ldg(a.totals) : a.ntiles;
+    const int64_t nbunches = BATCHED ? (int64_t)__ldg(a.totals + 1) : a.nbunches;
     int blk = blockIdx.x;
 
     if (blk < a.nblk_tiles) {
         // ---- re-arrangement of dirty tiles (Sec. 3.2, checking prediction):
         // the warps of this role stride over the tiles
         const int64_t nw = (int64_t)a.nblk_tiles * kCalibWarps;
-        for (int64_t t = (int64_t)blk * kCalibWarps + warp; t < a.ntiles; t += nw) {
+        for (int64_t t = (int64_t)blk * kCalibWarps + warp; t < ntiles; t += nw) {
             const uint32_t info = __ldg(a.tile_info + t);
-            if ((info & kInfoDirty) && !(info & kInfoResolved)) repair_dirty_tile<P>(a, t, info, lane);
+            if (!(info & kInfoDirty) || (info & kInfoResolved)) continue;
+            if constexpr (BATCHED) {
+                const int32_t mi = batch_matrix_of_tile(a.mats, a.count, t);
+                const BatchMat *mm = a.mats + mi;
+                const int32_t tb = __ldg(&mm->tile_base);
+                repair_dirty_tile<P>(ldg_ptr(&mm->row_ptr),
+                                     static_cast<Y *>(ldg_ptr(const_cast<void *const *>(&mm->y))),
+                                     a.tile_offset + tb + mi, __ldg(&mm->m), __ldg(&mm->nnz), a.L,
+                                     t - tb, info, a.err, lane);
+            } else {
+                repair_dirty_tile<P>(a.row_ptr, y, a.tile_offset, a.m, a.nnz, a.L, t, info, a.err,
+                                     lane);
+            }
         }
         return;
     }
@@ -722,13 +849,30 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
         // and a run that goes on past the window is finished by this warp.
         const double *sv = static_cast<const double *>(a.sync_val);
         const double *tv = static_cast<const double *>(a.tail_val);
+        // (in a batch, runs are keyed by matrix and row: bunches of different
+        // matrices never share a row)
+        auto key_of = [&](int64_t ww) -> int64_t {
+            const int64_t r = __ldg(a.sync_idx + ww);
+            if constexpr (BATCHED) return ((int64_t)__ldg(a.bunch_mat + ww) << 32) | r;
+            else return r;
+        };
         const int64_t base = ((int64_t)blk * kCalibWarps + warp) * 32;
         const int64_t w = base + lane;
-        const bool valid = w < a.nbunches;
-        const int32_t r = valid ? __ldg(a.sync_idx + w) : -1;
-        int32_t rprev = __shfl_up_sync(FULL, r, 1);
-        if (lane == 0) rprev = (valid && w > 0) ? __ldg(a.sync_idx + w - 1) : -1;
-        const bool lead = valid && (w == 0 || rprev != r);
+        const bool valid = w < nbunches;
+        const int64_t kw = valid ? key_of(w) : -1;
+        const int32_t r = (int32_t)(kw & 0xffffffff);
+        int64_t kprev = __shfl_up_sync(FULL, kw, 1);
+        if (lane == 0) kprev = (valid && w > 0) ? key_of(w - 1) : -1;
+        const bool lead = valid && (w == 0 || kprev != kw);
+        Y *__restrict__ yw = y;  // y and m of this lane's bunch's matrix
+        int32_t mw = a.m;
+        if constexpr (BATCHED) {
+            if (valid) {
+                const BatchMat *mm = a.mats + (kw >> 32);
+                yw = static_cast<Y *>(ldg_ptr(const_cast<void *const *>(&mm->y)));
+                mw = __ldg(&mm->m);
+            }
+        }
         const unsigned lmask = __ballot_sync(FULL, lead);
         if (lmask == 0) return;  // the whole window continues a run led earlier
         const int firstlead = __ffs(lmask) - 1;
@@ -749,43 +893,57 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
         const bool next_lead = __shfl_down_sync(FULL, lead, 1);
         const bool next_valid = __shfl_down_sync(FULL, valid, 1);
         if (lane < 31) next_same = next_valid && !next_lead;
-        else next_same = valid && w + 1 < a.nbunches && __ldg(a.sync_idx + w + 1) == r;
+        else next_same = valid && w + 1 < nbunches && key_of(w + 1) == kw;
         if (owned && !next_same) {
             const int64_t wl = base + first;  // the run's leader
             double total = C;
             if (wl > 0 && __ldg(a.tail_flag + wl - 1)) total += tv[wl - 1];
-            if (r >= 0 && r < a.m) y[r] = (Y)total;
+            if (r >= 0 && r < mw) yw[r] = (Y)total;
             else atomicOr(a.err, SSSPMV_DEV_RANGE);
         }
         const bool open = __shfl_sync(FULL, owned && next_same, 31);
         if (open) {  // the last run continues past the window (long rows)
-            const int32_t rr = __shfl_sync(FULL, r, 31);
+            const int64_t kk = __shfl_sync(FULL, kw, 31);
+            const int32_t rr = (int32_t)(kk & 0xffffffff);
             const double csum = __shfl_sync(FULL, C, 31);
             const int64_t wl = base + __shfl_sync(FULL, first, 31);
             double acc = 0.0;
             for (int64_t b2 = base + 32;; b2 += 32) {
                 const int64_t ww = b2 + lane;
-                const bool in = ww < a.nbunches && __ldg(a.sync_idx + ww) == rr;
+                const bool in = ww < nbunches && key_of(ww) == kk;
                 if (in) acc += sv[ww];
                 if (__popc(__ballot_sync(FULL, in)) < 32) break;
             }
 #pragma unroll
             for (int d = 16; d >= 1; d >>= 1) acc += __shfl_xor_sync(FULL, acc, d);
+            Y *__restrict__ yr =
+                reinterpret_cast<Y *>(__shfl_sync(FULL, (unsigned long long)yw, 31));
+            const int32_t mr = __shfl_sync(FULL, mw, 31);
             if (lane == 0) {
                 double total = csum + acc;
                 if (wl > 0 && __ldg(a.tail_flag + wl - 1)) total += tv[wl - 1];
-                if (rr >= 0 && rr < a.m) y[rr] = (Y)total;
+                if (rr >= 0 && rr < mr) yr[rr] = (Y)total;
                 else atomicOr(a.err, SSSPMV_DEV_RANGE);
             }
         }
         return;
     }
     blk -= a.nblk_sync;
-    // ---- rows before tile_offset[0] are empty and covered by no tile
-    const int32_t r0 = __ldg(a.tile_offset);
-    for (int64_t r = (int64_t)blk * blockDim.x + threadIdx.x; r < r0;
-         r += (int64_t)a.nblk_zero * blockDim.x)
-        y[r] = Y(0);
+    // ---- rows before tile_offset[0] are empty and covered by no tile (in
+    // a batch: each matrix's, the blocks striding over the matrices)
+    if constexpr (BATCHED) {
+        for (int32_t mi = blk; mi < a.count; mi += a.nblk_zero) {
+            const BatchMat *mm = a.mats + mi;
+            const int32_t r0 = __ldg(a.tile_offset + __ldg(&mm->tile_base) + mi);
+            Y *__restrict__ ym = static_cast<Y *>(ldg_ptr(const_cast<void *const *>(&mm->y)));
+            for (int32_t r = threadIdx.x; r < r0; r += blockDim.x) ym[r] = Y(0);
+        }
+    } else {
+        const int32_t r0 = __ldg(a.tile_offset);
+        for (int64_t r = (int64_t)blk * blockDim.x + threadIdx.x; r < r0;
+             r += (int64_t)a.nblk_zero * blockDim.x)
+            y[r] = Y(0);
+    }
 }
 
 }  // namespace ssspmv

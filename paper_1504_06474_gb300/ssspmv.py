@@ -26,6 +26,8 @@ SSSPMV_EDEVICE = -4
 SSSPMV_EUNSUPPORTED = -5
 SSSPMV_ETOOLARGE = -6
 SSSPMV_NOALLOC_SCRATCH_BYTES = 8 << 20
+SSSPMV_MAX_DIM = 2147483647 - 256
+SSSPMV_DEV_TIMEOUT, SSSPMV_DEV_RANGE, SSSPMV_DEV_CALIB, SSSPMV_DEV_BATCH = 1, 2, 4, 8
 
 
 class SsspmvError(RuntimeError):
@@ -71,6 +73,8 @@ _SIGS = {
     "ssspmv_plan_execute": (ctypes.c_int, [P, P, P, P, P, P, P]),
     "ssspmv_plan_workspace": (ctypes.c_int, [P, P, P]),
     "ssspmv_plan_destroy": (None, [P]),
+    "ssspmv_batched_workspace_bytes": (sz, [i32, i64, i32, OPTS]),
+    "ssspmv_csr_batched_f32": (ctypes.c_int, [i32, P, i64, OPTS, P, sz, P]),
     "ssspmv_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "ssspmv_last_cuda_error": (ctypes.c_int, []),
     "ssspmv_version": (ctypes.c_int, []),
@@ -305,6 +309,35 @@ def ssspmv_plan_workspace(plan):
 
 def ssspmv_plan_destroy(plan) -> None:
     _lib().ssspmv_plan_destroy(plan)
+
+
+class ssspmv_csr_desc(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("n", ctypes.c_int32), ("nnz", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("row_ptr", ctypes.c_void_p),
+                ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("y", ctypes.c_void_p)]
+
+
+def batch_descriptors(mats) -> bytes:
+    """Packs (m, n, nnz, row_ptr, col_idx, val, x, y) tuples (pointers or
+    tensors) into the bytes of a descriptor array, to be copied to the device."""
+    arr = (ssspmv_csr_desc * len(mats))()
+    for d, (m, n, nnz, rp, col, val, x, y) in zip(arr, mats):
+        d.m, d.n, d.nnz, d.reserved = m, n, nnz, 0
+        d.row_ptr, d.col_idx, d.val, d.x, d.y = _ptr(rp), _ptr(col), _ptr(val), _ptr(x), _ptr(y)
+    return bytes(arr)
+
+
+def ssspmv_batched_workspace_bytes(count, total_nnz, val_bytes=4, opts=None) -> int:
+    return int(_lib().ssspmv_batched_workspace_bytes(count, total_nnz, val_bytes, _opts(opts)))
+
+
+def ssspmv_csr_batched_f32(count, mats, total_nnz, opts=None, workspace=None, ws_bytes=None,
+                           stream=None) -> int:
+    if ws_bytes is None:
+        ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    return _lib().ssspmv_csr_batched_f32(count, _ptr(mats), total_nnz, _opts(opts),
+                                         _ptr(workspace), ws_bytes, _stream(stream))
 
 
 def ssspmv_strerror(code: int) -> str:

@@ -66,6 +66,10 @@ def _load():
         lib.synth_stencil27.argtypes = [i32, i32, i32, u64, P, P, P]
         lib.synth_rmat.restype = i64
         lib.synth_rmat.argtypes = [i32, i64, f64, f64, f64, u64, i64, P, P, P, i64, P]
+        lib.synth_banded.restype = i64
+        lib.synth_banded.argtypes = [i32, i32, u64, P, P, P]
+        lib.synth_range_rows_ptr.restype = i64
+        lib.synth_range_rows_ptr.argtypes = [i32, i32, i32, u64, P]
         _lib = lib
     return _lib
 
@@ -139,6 +143,76 @@ def rmat(scale: int, edge_factor: int = 16, abc=(0.57, 0.19, 0.19), seed: int = 
     empty = int(np.count_nonzero(np.diff(row_ptr) == 0))
     note = "injected row %d; %d of %d rows empty (%.1f%%)" % (inj.value, empty, m, 100.0 * empty / m)
     return CSR(m, m, row_ptr, col[:nnz], val[:nnz], name="rmat%d" % scale, note=note)
+
+
+def banded(m: int, k: int, seed: int) -> CSR:
+    """Half-bandwidth k: row r holds columns max(0, r-k) .. min(m-1, r+k)."""
+    lib = _load()
+    row_ptr = np.empty(m + 1, dtype=np.int32)
+    nnz = lib.synth_banded(m, k, seed, _p(row_ptr), None, None)
+    if nnz < 0:
+        raise MemoryError("synth_banded: nnz past int32")
+    col = np.empty(nnz, dtype=np.int32)
+    val = np.empty(nnz, dtype=np.float64)
+    lib.synth_banded(m, k, seed, _p(row_ptr), _p(col), _p(val))
+    return CSR(m, m, row_ptr, col, val, name="banded%d_k%d" % (m, k))
+
+
+def range_rows(m: int, lo: int, hi: int, seed: int) -> CSR:
+    """Row lengths uniform in {lo..hi}, sorted distinct uniform columns in [0, m)."""
+    lib = _load()
+    row_ptr = np.empty(m + 1, dtype=np.int32)
+    nnz = lib.synth_range_rows_ptr(m, lo, hi, seed, _p(row_ptr))
+    if nnz < 0:
+        raise MemoryError("synth_range_rows_ptr: nnz past int32")
+    col = np.empty(nnz, dtype=np.int32)
+    val = np.empty(nnz, dtype=np.float64)
+    lib.synth_fill_uniform(m, m, _p(row_ptr), seed, _p(col), _p(val))
+    return CSR(m, m, row_ptr, col, val, name="uniform%d_%d_%d" % (m, lo, hi))
+
+
+def rmat_clipped(m: int, edge_factor: int, seed: int) -> CSR:
+    """R-MAT (0.57, 0.19, 0.19, 0.05) at scale ceil(log2 m), edge factor
+    `edge_factor`, restricted to its leading m rows and columns."""
+    scale = max(1, int(np.ceil(np.log2(max(m, 2)))))
+    A = rmat(scale, edge_factor, (0.57, 0.19, 0.19), seed=seed)
+    rp = A.row_ptr[: m + 1].astype(np.int64)
+    col = A.col[: rp[-1]]
+    val = A.val[: rp[-1]]
+    keep = col < m
+    kept = np.concatenate([[0], np.cumsum(keep, dtype=np.int64)])
+    new_rp = kept[rp].astype(np.int32)
+    return CSR(m, m, new_rp, col[keep].copy(), val[keep].copy(), name="rmat%d_ef%d" % (m, edge_factor))
+
+
+BATCH_FAMILIES = ("banded", "uniform", "rmat")
+
+
+def batch_specs(count: int = 512, seed: int = 3, m_lo: int = 1000, m_hi: int = 200000):
+    """The seeded recipe of a mixed batch: per matrix (family, m, parameter,
+    seed) with m log-uniform in [m_lo, m_hi], the family drawn uniformly from
+    banded (half-bandwidth k ~ U{8..64}), uniform random (row lengths
+    U{4..40}) and R-MAT (edge factor 8, clipped to m)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    specs = []
+    for i in range(count):
+        fam = BATCH_FAMILIES[int(rng.integers(0, 3))]
+        m = int(round(float(np.exp(rng.uniform(np.log(m_lo), np.log(m_hi))))))
+        par = int(rng.integers(8, 65)) if fam == "banded" else (8 if fam == "rmat" else 0)
+        specs.append((fam, m, par, int(seed) * 100003 + i))
+    return specs
+
+
+def batch_matrix(spec) -> tuple[CSR, np.ndarray]:
+    """One matrix of a batch recipe with its x (U[-1, 1)), both FP64."""
+    fam, m, par, s = spec
+    if fam == "banded":
+        A = banded(m, par, s)
+    elif fam == "uniform":
+        A = range_rows(m, 4, 40, s)
+    else:
+        A = rmat_clipped(m, par, s)
+    return A, sym_vector(A.n, seed=s)
 
 
 def workload(name: str) -> tuple[CSR, np.ndarray]:

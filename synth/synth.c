@@ -303,3 +303,47 @@ int64_t synth_rmat(int32_t scale, int64_t nedges, double a, double b, double c,
     free(pos);
     return nnz;
 }
+
+/* ------------------------------------------------------------------ */
+/* Banded rows: row r holds every column in [max(0, r-k), min(m-1, r+k)] */
+/* (half-bandwidth k, 2k+1 entries in interior rows), values U[-1,1).   */
+/* col/val may be NULL to count only.  Returns nnz (or -1 past int32).  */
+int64_t synth_banded(int32_t m, int32_t k, uint64_t seed, int32_t *row_ptr, int32_t *col,
+                     double *val)
+{
+    int64_t acc = 0;
+    row_ptr[0] = 0;
+    for (int32_t r = 0; r < m; ++r) {
+        int64_t lo = (int64_t)r - k < 0 ? 0 : (int64_t)r - k;
+        int64_t hi = (int64_t)r + k > m - 1 ? m - 1 : (int64_t)r + k;
+        acc += hi - lo + 1;
+        if (acc > 0x7fffffffLL) return -1;
+        row_ptr[r + 1] = (int32_t)acc;
+    }
+    if (!col || !val) return acc;
+    #pragma omp parallel for schedule(static)
+    for (int32_t r = 0; r < m; ++r) {
+        int64_t lo = (int64_t)r - k < 0 ? 0 : (int64_t)r - k;
+        int64_t b = row_ptr[r], e = row_ptr[r + 1];
+        for (int64_t q = b; q < e; ++q) col[q] = (int32_t)(lo + (q - b));
+    }
+    #pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < acc; ++q)
+        val[q] = sym(seed, ST_VAL, (uint64_t)q);
+    return acc;
+}
+
+/* Row lengths uniform in {lo..hi} (no forced empty rows); writes         */
+/* row_ptr[m+1] and returns nnz (or -1 past int32).  Fill the columns and */
+/* values with synth_fill_uniform.                                       */
+int64_t synth_range_rows_ptr(int32_t m, int32_t lo, int32_t hi, uint64_t seed, int32_t *row_ptr)
+{
+    int64_t acc = 0;
+    row_ptr[0] = 0;
+    for (int32_t r = 0; r < m; ++r) {
+        acc += lo + (int64_t)below(seed, ST_LEN, (uint64_t)r, (uint64_t)(hi - lo + 1));
+        if (acc > 0x7fffffffLL) return -1;
+        row_ptr[r + 1] = (int32_t)acc;
+    }
+    return acc;
+}

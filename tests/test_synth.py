@@ -52,3 +52,33 @@ def test_vectors_deterministic():
     c = synth.sym_vector(1000, seed=5)
     assert np.array_equal(a, b) and not np.array_equal(a, c)
     assert a.min() >= -1.0 and a.max() < 1.0
+
+
+def test_banded_exact_columns():
+    A = synth.banded(50, 7, seed=4)
+    for r in range(50):
+        cols = A.col[A.row_ptr[r]:A.row_ptr[r + 1]]
+        assert list(cols) == list(range(max(0, r - 7), min(49, r + 7) + 1))
+    assert A.nnz == sum(min(49, r + 7) - max(0, r - 7) + 1 for r in range(50))
+
+
+def test_range_rows_and_clipped_rmat():
+    B = synth.range_rows(3000, 4, 40, seed=5)
+    L = np.diff(B.row_ptr)
+    assert L.min() >= 4 and L.max() <= 40
+    for r in (0, 1234, 2999):
+        c = B.col[B.row_ptr[r]:B.row_ptr[r + 1]]
+        assert np.all(np.diff(c) > 0) and c.max() < 3000
+    C = synth.rmat_clipped(1500, 8, seed=6)
+    assert C.m == C.n == 1500 and C.col.max() < 1500 and np.all(np.diff(C.row_ptr) >= 0)
+    C2 = synth.rmat_clipped(1500, 8, seed=6)
+    assert np.array_equal(C.col, C2.col) and np.array_equal(C.val, C2.val)
+
+
+def test_batch_recipe():
+    sp = synth.batch_specs(512, seed=3)
+    assert sp == synth.batch_specs(512, seed=3)
+    ms = np.array([s[1] for s in sp])
+    assert ms.min() >= 1000 and ms.max() <= 200000
+    assert {s[0] for s in sp} == set(synth.BATCH_FAMILIES)
+    assert all(8 <= s[2] <= 64 for s in sp if s[0] == "banded")
