@@ -1,7 +1,13 @@
 """Benchmark: CSR SpMV by speculative segmented sum on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload stencil160] [--tile-w 0] [--tile-s 0] [--e2e-steps 20]
+                    [--workload stencil160|rmat22|batch512|...] [--precision f64|f32|bf16]
+                    [--tile-w 0] [--tile-s 0] [--variant 0] [--e2e-steps 10]
+
+--precision f32/bf16 times ssspmv_csr_f32 / ssspmv_csr_bf16f32 on the workload
+and the plain FP64 call beside it; --workload batch<count> times the batched
+FP32 call over a seeded mixed batch as one CUDA-graph replay, beside the same
+matrices as separate FP32 calls and separate plain FP64 calls.
 
 A step is one full y = A x through ssspmv_csr_f64 (kernels (a) partition,
 (b) segmented sum, (c) calibration) on the synthetic 27-point stencil over a
@@ -357,6 +363,333 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# reduced precision (FP32 val/x/y, or BF16 val with FP32 x/y) on one matrix
+
+def _timed_loop(step, flush_l2, K, stream):
+    """K steps, each after an L2 flush outside the timed region; returns the
+    per-step device times (ms) from events on the launching stream."""
+    import torch
+    times = []
+    for _ in range(K):
+        flush_l2()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times
+
+
+def _flusher(dev):
+    import torch
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    sink = torch.empty(1, dtype=torch.int64, device=dev)
+
+    def flush_l2():
+        flush.fill_(1)
+        torch.sum(flush.view(torch.int64), 0, keepdim=True, out=sink)
+    return flush_l2
+
+
+def _cpu_baseline(mats, budget_s, bytes_of):
+    """The oracle (FP64 row loop over OpenMP threads) on a bounded sample of
+    the workload; GB/s in this workload's own byte count."""
+    import numpy as np
+
+    import oracle
+    t0, done, nbytes, used, k = time.perf_counter(), 0, 0, 1, 0
+    while time.perf_counter() - t0 < budget_s:
+        A, x = mats[k % len(mats)]
+        y = np.empty(A.m)
+        _, used = oracle.spmv_omp(A.row_ptr, A.col, A.val, x, y=y)
+        nbytes += bytes_of(A)
+        done += 1
+        k += 1
+    dt = time.perf_counter() - t0
+    return nbytes / dt / 1e9, used, done, dt
+
+
+def run_precision(args):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1504_06474_gb300 import _build
+    from paper_1504_06474_gb300 import ssspmv as C
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _build.build()
+    A, x = synth.workload(args.workload)
+    vb = 4 if args.precision == "f32" else 2
+    rp = torch.as_tensor(A.row_ptr, device=dev)
+    col = torch.as_tensor(A.col, device=dev)
+    if vb == 4:
+        val = torch.as_tensor(A.val.astype(np.float32), device=dev)
+        fn = C.ssspmv_csr_f32
+    else:
+        val = torch.as_tensor(A.val).to(torch.bfloat16).to(dev).view(torch.int16)
+        fn = C.ssspmv_csr_bf16f32
+    xd = torch.as_tensor(x.astype(np.float32), device=dev)
+    y = torch.empty(A.m, dtype=torch.float32, device=dev)
+    opts = C.make_opts(W=args.tile_w, S=args.tile_s, variant=args.variant)
+    ws = torch.empty(C.ssspmv_workspace_bytes(A.m, A.nnz, vb, opts), dtype=torch.uint8,
+                     device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush_l2 = _flusher(dev)
+
+    def step():
+        C.check(fn(A.m, A.n, A.nnz, rp, col, val, xd, y, opts=opts, workspace=ws,
+                   stream=stream), "reduced-precision call")
+    for _ in range(args.warmup):
+        step()
+    K = args.steps
+    timer = C.ssspmv_timer_create(K)
+    opts_t = C.make_opts(W=args.tile_w, S=args.tile_s, variant=args.variant, timer=timer)
+
+    def step_t():
+        C.check(fn(A.m, A.n, A.nnz, rp, col, val, xd, y, opts=opts_t, workspace=ws,
+                   stream=stream), "reduced-precision call")
+    sampler = ClockSampler(local)
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    time.sleep(0.25)
+    _timed_loop(step_t, flush_l2, K, stream)
+    clocks = sampler.stop()
+    t = C.ssspmv_timer_read(timer, K)
+    C.ssspmv_timer_destroy(timer)
+    whole = sum(v[3] for v in t) / K
+    seg = sum(v[1] for v in t) / K
+    nbytes = algorithmic_bytes(A.m, A.n, A.nnz, val_bytes=vb, y_bytes=4, x_bytes=4)
+    value = nbytes / (whole / 1e3) / 1e9
+    # the plain FP64 call on the same matrix, same GPU, same timing
+    rp64, col64 = rp, col
+    val64 = torch.as_tensor(A.val, device=dev)
+    x64 = torch.as_tensor(x, device=dev)
+    y64 = torch.empty(A.m, dtype=torch.float64, device=dev)
+    ws64 = torch.empty(C.ssspmv_workspace_bytes(A.m, A.nnz, 8, None), dtype=torch.uint8,
+                       device=dev)
+
+    def step64():
+        C.check(C.ssspmv_csr_f64(A.m, A.n, A.nnz, rp64, col64, val64, x64, y64, workspace=ws64,
+                                 stream=stream), "ssspmv_csr_f64")
+    for _ in range(args.warmup):
+        step64()
+    t64 = _timed_loop(step64, flush_l2, min(K, 200), stream)
+    ms64 = sum(t64) / len(t64)
+    # end to end: pinned host inputs in, y out, every step
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        h = [pin(A.row_ptr), pin(A.col), val.cpu().pin_memory(), pin(x.astype(np.float32))]
+        d = [rp, col, val, xd]
+        hy = torch.empty(A.m, dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for dst, src in zip(d, h):
+                dst.copy_(src, non_blocking=True)
+            step()
+            hy.copy_(y, non_blocking=True)
+            torch.cuda.synchronize(dev)
+        te = (time.perf_counter() - t0) / args.e2e_steps
+        h2d = sum(v.numel() * v.element_size() for v in h)
+        e2e = {"value": round(nbytes / te / 1e9, 3), "unit": "GB/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": A.m * 4, "ms_per_step": round(te * 1e3, 4)}
+    status = C.ssspmv_device_status(ws, stream=stream)
+    if status:
+        raise RuntimeError("device status bits %#x" % status)
+    cpu = None
+    if args.cpu_seconds > 0:
+        rate, used, reps, dt = _cpu_baseline([(A, x)], args.cpu_seconds,
+                                             lambda M: nbytes)
+        cpu = {"value": round(rate, 3), "unit": "GB/s", "cores": used, "kind": "oracle",
+               "sample": "%d whole %s SpMVs by the FP64 oracle row loop (%d OpenMP threads), "
+                         "counted at this configuration's bytes per step, %.1f s"
+                         % (reps, args.workload, used, dt)}
+    hbm, peak_kind = peaks()
+    shape = C.ssspmv_plan_shape(A.m, A.nnz, vb, opts)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": 1, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(whole, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if vb == 4 else "bf16-val/f32", "data": "synthetic",
+        "config": {"workload": args.workload, "precision": args.precision, "m": A.m,
+                   "n": A.n, "nnz": A.nnz, "W": shape["W"], "S": shape["S"],
+                   "bytes_per_step": nbytes, "hbm_frac": round(value / hbm, 4),
+                   "accumulation": "compensated FP32 pairs (TwoProduct + TwoSum)",
+                   "stage_ms": {"partition": round(sum(v[0] for v in t) / K, 5),
+                                "segsum": round(seg, 5),
+                                "calibrate": round(sum(v[2] for v in t) / K, 5)},
+                   "plain_f64_ms": round(ms64, 5), "speedup_vs_plain_f64": round(ms64 / whole, 3),
+                   "l2": "flushed between steps (512 MB write then read, outside the timed events)"},
+        "roofline": {"bound": "hbm", "kernel": "segsum_kernel",
+                     "achieved": round(nbytes / (seg / 1e3) / 1e9, 2), "peak": hbm,
+                     "unit": "GB/s", "frac": round(nbytes / (seg / 1e3) / 1e9 / hbm, 4),
+                     "peak_kind": peak_kind, "traffic": None},
+        "clocks": clocks, "e2e": e2e, "gpu_launches": 3 * K, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# a batch of many matrices (FP32) in one graph launch
+
+def run_batch(args):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1504_06474_gb300 import _build
+    from paper_1504_06474_gb300 import ssspmv as C
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _build.build()
+    count = int(args.workload[len("batch"):])
+    specs = synth.batch_specs(count, seed=3)
+    t_gen = time.perf_counter()
+    mats = [synth.batch_matrix(sp) for sp in specs]
+    t_gen = time.perf_counter() - t_gen
+    dd = []  # device arrays per matrix
+    descs = []
+    for A, x in mats:
+        d = dict(rp=torch.as_tensor(A.row_ptr, device=dev), col=torch.as_tensor(A.col, device=dev),
+                 val=torch.as_tensor(A.val.astype(np.float32), device=dev),
+                 x=torch.as_tensor(x.astype(np.float32), device=dev),
+                 y=torch.empty(A.m, dtype=torch.float32, device=dev))
+        dd.append(d)
+        descs.append((A.m, A.n, A.nnz, d["rp"], d["col"], d["val"], d["x"], d["y"]))
+    desc = torch.as_tensor(np.frombuffer(C.batch_descriptors(descs), np.uint8).copy(), device=dev)
+    total_nnz = sum(A.nnz for A, _ in mats)
+    f32_bytes = lambda A: algorithmic_bytes(A.m, A.n, A.nnz, val_bytes=4, y_bytes=4, x_bytes=4)
+    nbytes = sum(f32_bytes(A) for A, _ in mats)
+    opts = C.make_opts(W=args.tile_w, S=args.tile_s, variant=args.variant)
+    ws = torch.empty(C.ssspmv_batched_workspace_bytes(count, total_nnz, 4, opts),
+                     dtype=torch.uint8, device=dev)
+    s = torch.cuda.Stream(dev)
+    flush_l2 = _flusher(dev)
+    torch.cuda.synchronize(dev)
+
+    def batched(o=opts):
+        C.check(C.ssspmv_csr_batched_f32(count, desc, total_nnz, opts=o, workspace=ws, stream=s),
+                "ssspmv_csr_batched_f32")
+    with torch.cuda.stream(s):
+        for _ in range(args.warmup):
+            batched()
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        batched()
+    K = args.steps
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.25)
+    with torch.cuda.stream(s):
+        times = _timed_loop(g.replay, flush_l2, K, s)
+    clocks = sampler.stop()
+    ms = sum(times) / K
+    value = nbytes / (ms / 1e3) / 1e9
+    # stage split from direct (uncaptured) launches with the library's timer
+    kst = min(K, 20)
+    timer = C.ssspmv_timer_create(kst)
+    ot = C.make_opts(W=args.tile_w, S=args.tile_s, variant=args.variant, timer=timer)
+    with torch.cuda.stream(s):
+        _timed_loop(lambda: batched(ot), flush_l2, kst, s)
+    st = C.ssspmv_timer_read(timer, kst)
+    C.ssspmv_timer_destroy(timer)
+    seg = sum(v[1] for v in st) / kst
+    stage = {"setup_and_partition": round(sum(v[0] for v in st) / kst, 5), "segsum": round(seg, 5),
+             "calibrate": round(sum(v[2] for v in st) / kst, 5)}
+    # the same matrices as separate single calls: FP32, and the plain FP64 kernel
+    big = max(C.ssspmv_workspace_bytes(A.m, A.nnz, 8, None) for A, _ in mats)
+    ws1 = torch.empty(big, dtype=torch.uint8, device=dev)
+
+    def separate_f32():
+        for (A, _), d in zip(mats, dd):
+            C.check(C.ssspmv_csr_f32(A.m, A.n, A.nnz, d["rp"], d["col"], d["val"], d["x"], d["y"],
+                                     workspace=ws1, stream=s), "ssspmv_csr_f32")
+    with torch.cuda.stream(s):
+        separate_f32()
+        t_sep = _timed_loop(separate_f32, flush_l2, 5, s)
+    d64 = [dict(val=torch.as_tensor(A.val, device=dev), x=torch.as_tensor(x, device=dev),
+                y=torch.empty(A.m, dtype=torch.float64, device=dev)) for A, x in mats]
+
+    def separate_f64():
+        for (A, _), d, e in zip(mats, dd, d64):
+            C.check(C.ssspmv_csr_f64(A.m, A.n, A.nnz, d["rp"], d["col"], e["val"], e["x"], e["y"],
+                                     workspace=ws1, stream=s), "ssspmv_csr_f64")
+    with torch.cuda.stream(s):
+        separate_f64()
+        t64 = _timed_loop(separate_f64, flush_l2, 5, s)
+    del d64
+    ms_sep, ms64 = sum(t_sep) / len(t_sep), sum(t64) / len(t64)
+    # end to end: every matrix's inputs from pinned host memory, the graph, every y back
+    e2e = None
+    if args.e2e_steps > 0:
+        hosts = [(torch.from_numpy(A.row_ptr).pin_memory(), torch.from_numpy(A.col).pin_memory(),
+                  d["val"].cpu().pin_memory(), d["x"].cpu().pin_memory(),
+                  torch.empty(A.m, dtype=torch.float32).pin_memory()) for (A, _), d in zip(mats, dd)]
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            with torch.cuda.stream(s):
+                for h, d in zip(hosts, dd):
+                    d["rp"].copy_(h[0], non_blocking=True)
+                    d["col"].copy_(h[1], non_blocking=True)
+                    d["val"].copy_(h[2], non_blocking=True)
+                    d["x"].copy_(h[3], non_blocking=True)
+                g.replay()
+                for h, d in zip(hosts, dd):
+                    h[4].copy_(d["y"], non_blocking=True)
+            s.synchronize()
+        te = (time.perf_counter() - t0) / args.e2e_steps
+        h2d = sum(sum(v.numel() * v.element_size() for v in h[:4]) for h in hosts)
+        d2h = sum(h[4].numel() * 4 for h in hosts)
+        e2e = {"value": round(nbytes / te / 1e9, 3), "unit": "GB/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": round(te * 1e3, 4)}
+    status = C.ssspmv_device_status(ws, stream=s)
+    if status:
+        raise RuntimeError("device status bits %#x" % status)
+    cpu = None
+    if args.cpu_seconds > 0:
+        rate, used, done, dt = _cpu_baseline(mats, args.cpu_seconds, f32_bytes)
+        cpu = {"value": round(rate, 3), "unit": "GB/s", "cores": used, "kind": "oracle",
+               "sample": "%d matrix products cycling through the batch in order, by the FP64 "
+                         "oracle row loop (%d OpenMP threads), counted at FP32 bytes, %.1f s"
+                         % (done, used, dt)}
+    hbm, peak_kind = peaks()
+    fams = {f: sum(1 for sp in specs if sp[0] == f) for f in synth.BATCH_FAMILIES}
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": 1, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "matrices": count, "families": fams,
+                   "rows": sum(A.m for A, _ in mats), "nnz": total_nnz,
+                   "bytes_per_step": nbytes, "hbm_frac": round(value / hbm, 4),
+                   "W": C.ssspmv_plan_shape(1, 1, 4, opts)["W"],
+                   "launch": "one CUDA graph replay: set-up, partition, one persistent "
+                             "segmented-sum launch over every bunch of every matrix, calibration",
+                   "stage_ms": stage, "separate_f32_calls_ms": round(ms_sep, 4),
+                   "speedup_vs_separate_f32_calls": round(ms_sep / ms, 3),
+                   "separate_plain_f64_calls_ms": round(ms64, 4),
+                   "speedup_vs_plain_f64": round(ms64 / ms, 3),
+                   "generation_s": round(t_gen, 1),
+                   "l2": "flushed between steps (512 MB write then read, outside the timed events)"},
+        "roofline": {"bound": "hbm", "kernel": "segsum_kernel (batched)",
+                     "achieved": round(nbytes / (seg / 1e3) / 1e9, 2), "peak": hbm,
+                     "unit": "GB/s", "frac": round(nbytes / (seg / 1e3) / 1e9 / hbm, 4),
+                     "peak_kind": peak_kind, "traffic": None},
+        "clocks": clocks, "e2e": e2e, "gpu_launches": 4 * K, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -370,11 +703,17 @@ def main():
                     help="0 default, 1 speculative + calibration, 2 exact stores")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--precision", choices=["f64", "f32", "bf16"], default="f64",
+                    help="f32: FP32 val/x/y; bf16: BF16 val, FP32 x/y (compensated FP32 sums)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload.startswith("batch"):
+        return run_batch(args)
+    if args.precision != "f64":
+        return run_precision(args)
     return run_ours(args)
 
 
