@@ -82,12 +82,21 @@ extern "C" {
 #define SSSPMV_VARIANT_DEFAULT     0
 #define SSSPMV_VARIANT_SPECULATIVE 1
 #define SSSPMV_VARIANT_EXACT       2
+/*  ROWS         not the paper's method but the row-parallel CSR kernels it
+ *               compares against (Sec. 2.2), offered as a class for the
+ *               variant selector: a group of opts->W lanes per row (1 = the
+ *               scalar kernel, 2..32 powers of two = the vector kernel; 0 =
+ *               from the mean row length).  No partition and no calibration;
+ *               FP64 single calls only (the FP32/BF16, plan and batched entry
+ *               points return SSSPMV_EUNSUPPORTED). */
+#define SSSPMV_VARIANT_ROWS        3
 
 /* Tile and launch parameters (Sec. 3.1, Table 3).  Zero-initialise and set
  * only what you need; a NULL opts pointer means all defaults. */
 typedef struct ssspmv_opts {
     int32_t W;         /* entries per lane (odd, see ssspmv_supported_w); L = 32*W.
-                          0 = the shortest compiled tile */
+                          0 = the shortest compiled tile.  With SSSPMV_VARIANT_ROWS:
+                          lanes per row (see there) */
     int32_t S;         /* tiles per thread-bunch (warp); 0 = 4.  Each warp of a
                           persistent grid first takes an even contiguous share of
                           3/4 of the bunches, then single bunches from a counter */
@@ -225,6 +234,44 @@ size_t ssspmv_batched_workspace_bytes(int32_t count, int64_t total_nnz, int32_t 
 int ssspmv_csr_batched_f32(int32_t count, const ssspmv_csr_desc *mats, int64_t total_nnz,
                            const ssspmv_opts *opts, void *workspace, size_t ws_bytes,
                            void *stream);
+
+/* Learned variant selector (not in the paper; it only chooses among the
+ * kernels above and never changes their arithmetic).
+ *   ssspmv_features  16 statistics of row_ptr alone, each of order one, into
+ *     device float[16] (one pass over the rows twice, then one thread):
+ *     log2 m, log2 nnz, log2 mean row length, coefficient of variation of the
+ *     lengths, log2 max length, fractions of empty rows, of rows <= 4, of
+ *     rows >= 2x the mean, of entries in rows > 1024, median / 90th / 99th
+ *     percentile of log2 lengths, fraction of neighbours differing > 2x,
+ *     log2 rows per 480-entry tile, fraction of empty rows after an empty
+ *     row, fraction of entries in rows >= 32x the mean.  `scratch`: device
+ *     memory of ssspmv_features_scratch_bytes().
+ *   A perceptron F -> H1 -> H2 -> K (ReLU, ReLU, linear), FP32, parameters in
+ *   one device array (ssspmv_mlp_param_count floats: W1[H1][F], b1[H1],
+ *   W2[H2][H1], b2[H2], W3[K][H2], b3[K]), batch X[B][F] row-major; `scratch`
+ *   holds ssspmv_mlp_scratch_floats(B, ...) floats.
+ *   ssspmv_mlp_forward   out[B][K] (NULL: leave it in scratch).
+ *   ssspmv_mlp_backward  forward, then the gradient of the mean squared error
+ *     against target[B][K] (NaN targets count as 0 error) into grad (same
+ *     layout as params) and the loss into *loss (device float, may be NULL).
+ *   ssspmv_mlp_adam      one Adam step (Kingma & Ba) with L2 weight decay.
+ *   ssspmv_mlp_select    cls[b] = argmin over k of the predicted out[b][k].
+ * All asynchronous on `stream`; deterministic (fixed reduction orders). */
+size_t ssspmv_features_scratch_bytes(void);
+int ssspmv_features(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr, float *features,
+                    void *scratch, void *stream);
+int64_t ssspmv_mlp_param_count(int32_t F, int32_t H1, int32_t H2, int32_t K);
+size_t ssspmv_mlp_scratch_floats(int32_t B, int32_t F, int32_t H1, int32_t H2, int32_t K);
+int ssspmv_mlp_forward(const float *params, const float *X, int32_t B, int32_t F, int32_t H1,
+                       int32_t H2, int32_t K, float *scratch, float *out, void *stream);
+int ssspmv_mlp_backward(const float *params, const float *X, const float *target, int32_t B,
+                        int32_t F, int32_t H1, int32_t H2, int32_t K, float *scratch, float *grad,
+                        float *loss, void *stream);
+int ssspmv_mlp_adam(float *params, const float *grad, float *m1, float *m2, int64_t n, float lr,
+                    float beta1, float beta2, float eps, float weight_decay, int32_t step,
+                    void *stream);
+int ssspmv_mlp_select(const float *params, const float *X, int32_t B, int32_t F, int32_t H1,
+                      int32_t H2, int32_t K, float *scratch, int32_t *cls, void *stream);
 
 /* Allocation-free FP64 product.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- code handed

@@ -23,6 +23,9 @@ int f32_run(Call &c);
 int bf16_supported_w(int32_t *out, int cap);
 int bf16_resolve(Layout &l, int32_t S_opt);
 int bf16_run(Call &c);
+int run_rows_f64(const Call &c, int group);  // rows.cu
+int f32_run_batched(int32_t count, const void *desc, const BatchLayout &l, unsigned char *ws,
+                    cudaStream_t stream, int exact, int block_warps, cudaEvent_t *ev);  // batched.cu
 
 // one entry per stored value type; the value size identifies the precision
 struct Prec {
@@ -105,8 +108,20 @@ static int make_layout(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_o
     if (m < 0 || nnz < 0) return SSSPMV_EINVAL;
     // the kernels index rows and entries in 32 bits with up to 256 of headroom
     if (m > SSSPMV_MAX_DIM || nnz > SSSPMV_MAX_DIM) return SSSPMV_EINVAL;
-    if (o && (o->S < 0 || o->block_warps < 0 || o->variant < 0 || o->variant > 2))
+    if (o && (o->S < 0 || o->block_warps < 0 || o->variant < 0 || o->variant > 3))
         return SSSPMV_EINVAL;
+    if (o && o->variant == SSSPMV_VARIANT_ROWS) {
+        // row-parallel kernels: W is the lanes per row; the workspace holds
+        // only the error word
+        if (val_bytes != 8) return SSSPMV_EUNSUPPORTED;
+        if (o->W < 0 || o->W > 32 || (o->W & (o->W - 1))) return SSSPMV_EINVAL;
+        l.W = o->W;
+        l.L = 0;
+        l.ntiles = 0;
+        l.nbunch_cap = 0;
+        carve(l);
+        return SSSPMV_OK;
+    }
     int32_t W = 0;
     int rc = resolve_w(m, nnz, val_bytes, o, &W);
     if (rc) return rc;
@@ -220,6 +235,23 @@ static int run_call(int32_t val_bytes, int32_t m, int32_t n, int32_t nnz,
         if (rc) return rc;
     }
     if (ws_bytes < l.total || ((uintptr_t)ws & 255u)) return SSSPMV_EWORKSPACE;
+    if (opts && opts->variant == SSSPMV_VARIANT_ROWS) {
+        if (dbg_desc || dbg_yspec) return SSSPMV_EINVAL;  // no tiles to export
+        Call c;
+        c.m = m;
+        c.n = n;
+        c.nnz = nnz;
+        c.row_ptr = row_ptr;
+        c.col = col;
+        c.val = val;
+        c.x = x;
+        c.y = y;
+        c.lay = l;
+        c.ws = static_cast<unsigned char *>(ws);
+        c.stream = static_cast<cudaStream_t>(stream);
+        c.ev = opts->timer ? timer_next_slot(static_cast<ssspmv_timer *>(opts->timer)) : nullptr;
+        return run_rows_f64(c, l.W);
+    }
     rc = pr->resolve(l, opts ? opts->S : 0);
     if (rc) return rc;
     if (l.nbunches > l.nbunch_cap) return SSSPMV_EWORKSPACE;
@@ -261,9 +293,6 @@ __global__ void validate_kernel(int32_t m, int32_t n, int32_t nnz, const int32_t
         if (c < 0 || c >= n) atomicOr(bad, 4u);
     }
 }
-
-int f32_run_batched(int32_t count, const void *desc, const BatchLayout &l, unsigned char *ws,
-                    cudaStream_t stream, int exact, int block_warps, cudaEvent_t *ev);  // batched.cu
 
 }  // namespace ssspmv
 
@@ -368,6 +397,14 @@ int ssspmv_plan_shape(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_op
     Layout l;
     int rc = make_layout(m, nnz, val_bytes, opts, l);
     if (rc) return rc;
+    if (opts && opts->variant == SSSPMV_VARIANT_ROWS) {
+        if (W) *W = l.W;  // lanes per row (0: chosen per call from nnz/m)
+        if (L) *L = 0;
+        if (S) *S = 0;
+        if (ntiles) *ntiles = 0;
+        if (nbunches) *nbunches = 0;
+        return SSSPMV_OK;
+    }
     rc = pr->resolve(l, opts ? opts->S : 0);
     if (rc) return rc;
     if (W) *W = l.W;
@@ -417,6 +454,7 @@ static int make_batch_layout(int32_t count, int64_t total_nnz, int32_t val_bytes
                              const ssspmv_opts *o, BatchLayout &l)
 {
     if (count < 0 || total_nnz < 0) return SSSPMV_EINVAL;
+    if (o && o->variant == SSSPMV_VARIANT_ROWS) return SSSPMV_EUNSUPPORTED;
     if (o && (o->S < 0 || o->block_warps < 0 || o->variant < 0 || o->variant > 2))
         return SSSPMV_EINVAL;
     int32_t W = 0;
@@ -482,6 +520,7 @@ int ssspmv_plan_create(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr
     if (m < 0 || n < 0 || nnz < 0 || (m == 0 && nnz != 0)) return SSSPMV_EINVAL;
     if (m > 0 && !row_ptr) return SSSPMV_EINVAL;
     if (opts && opts->timer) return SSSPMV_EINVAL;  // time executions, not the plan
+    if (opts && opts->variant == SSSPMV_VARIANT_ROWS) return SSSPMV_EUNSUPPORTED;
     Layout l;
     int rc = make_layout(m, nnz, val_bytes, opts, l);
     if (rc) return rc;

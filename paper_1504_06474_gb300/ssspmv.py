@@ -74,6 +74,15 @@ _SIGS = {
     "ssspmv_plan_workspace": (ctypes.c_int, [P, P, P]),
     "ssspmv_plan_destroy": (None, [P]),
     "ssspmv_batched_workspace_bytes": (sz, [i32, i64, i32, OPTS]),
+    "ssspmv_features_scratch_bytes": (sz, []),
+    "ssspmv_features": (ctypes.c_int, [i32, i32, i32, P, P, P, P]),
+    "ssspmv_mlp_param_count": (i64, [i32, i32, i32, i32]),
+    "ssspmv_mlp_scratch_floats": (sz, [i32, i32, i32, i32, i32]),
+    "ssspmv_mlp_forward": (ctypes.c_int, [P, P, i32, i32, i32, i32, i32, P, P, P]),
+    "ssspmv_mlp_backward": (ctypes.c_int, [P, P, P, i32, i32, i32, i32, i32, P, P, P, P]),
+    "ssspmv_mlp_adam": (ctypes.c_int, [P, P, P, P, i64, ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_float, ctypes.c_float, ctypes.c_float, i32, P]),
+    "ssspmv_mlp_select": (ctypes.c_int, [P, P, i32, i32, i32, i32, i32, P, P, P]),
     "ssspmv_csr_batched_f32": (ctypes.c_int, [i32, P, i64, OPTS, P, sz, P]),
     "ssspmv_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "ssspmv_last_cuda_error": (ctypes.c_int, []),
@@ -131,7 +140,7 @@ def _stream(s):
     return s.cuda_stream
 
 
-VARIANT_DEFAULT, VARIANT_SPECULATIVE, VARIANT_EXACT = 0, 1, 2
+VARIANT_DEFAULT, VARIANT_SPECULATIVE, VARIANT_EXACT, VARIANT_ROWS = 0, 1, 2, 3
 
 
 def make_opts(W: int = 0, S: int = 0, timer=None, variant: int = 0,
@@ -338,6 +347,45 @@ def ssspmv_csr_batched_f32(count, mats, total_nnz, opts=None, workspace=None, ws
         ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     return _lib().ssspmv_csr_batched_f32(count, _ptr(mats), total_nnz, _opts(opts),
                                          _ptr(workspace), ws_bytes, _stream(stream))
+
+
+def ssspmv_features_scratch_bytes() -> int:
+    return int(_lib().ssspmv_features_scratch_bytes())
+
+
+def ssspmv_features(m, n, nnz, row_ptr, features, scratch, stream=None) -> int:
+    return _lib().ssspmv_features(m, n, nnz, _ptr(row_ptr), _ptr(features), _ptr(scratch),
+                                  _stream(stream))
+
+
+def ssspmv_mlp_param_count(F, H1, H2, K) -> int:
+    return int(_lib().ssspmv_mlp_param_count(F, H1, H2, K))
+
+
+def ssspmv_mlp_scratch_floats(B, F, H1, H2, K) -> int:
+    return int(_lib().ssspmv_mlp_scratch_floats(B, F, H1, H2, K))
+
+
+def ssspmv_mlp_forward(params, X, B, F, H1, H2, K, scratch, out=None, stream=None) -> int:
+    return _lib().ssspmv_mlp_forward(_ptr(params), _ptr(X), B, F, H1, H2, K, _ptr(scratch),
+                                     _ptr(out), _stream(stream))
+
+
+def ssspmv_mlp_backward(params, X, target, B, F, H1, H2, K, scratch, grad, loss=None,
+                        stream=None) -> int:
+    return _lib().ssspmv_mlp_backward(_ptr(params), _ptr(X), _ptr(target), B, F, H1, H2, K,
+                                      _ptr(scratch), _ptr(grad), _ptr(loss), _stream(stream))
+
+
+def ssspmv_mlp_adam(params, grad, m1, m2, n, lr, beta1=0.9, beta2=0.999, eps=1e-8,
+                    weight_decay=0.0, step=1, stream=None) -> int:
+    return _lib().ssspmv_mlp_adam(_ptr(params), _ptr(grad), _ptr(m1), _ptr(m2), n, lr, beta1,
+                                  beta2, eps, weight_decay, step, _stream(stream))
+
+
+def ssspmv_mlp_select(params, X, B, F, H1, H2, K, scratch, cls, stream=None) -> int:
+    return _lib().ssspmv_mlp_select(_ptr(params), _ptr(X), B, F, H1, H2, K, _ptr(scratch),
+                                    _ptr(cls), _stream(stream))
 
 
 def ssspmv_strerror(code: int) -> str:

@@ -70,6 +70,8 @@ def _load():
         lib.synth_banded.argtypes = [i32, i32, u64, P, P, P]
         lib.synth_range_rows_ptr.restype = i64
         lib.synth_range_rows_ptr.argtypes = [i32, i32, i32, u64, P]
+        lib.synth_blockdiag.restype = i64
+        lib.synth_blockdiag.argtypes = [i32, i32, i32, u64, P, P, P]
         _lib = lib
     return _lib
 
@@ -183,6 +185,37 @@ def rmat_clipped(m: int, edge_factor: int, seed: int) -> CSR:
     kept = np.concatenate([[0], np.cumsum(keep, dtype=np.int64)])
     new_rp = kept[rp].astype(np.int32)
     return CSR(m, m, new_rp, col[keep].copy(), val[keep].copy(), name="rmat%d_ef%d" % (m, edge_factor))
+
+
+def blockdiag(m: int, bmin: int, bmax: int, seed: int) -> CSR:
+    """Dense diagonal blocks of sizes U{bmin..bmax}."""
+    lib = _load()
+    row_ptr = np.empty(m + 1, dtype=np.int32)
+    nnz = lib.synth_blockdiag(m, bmin, bmax, seed, _p(row_ptr), None, None)
+    if nnz < 0:
+        raise MemoryError("synth_blockdiag: nnz past int32")
+    col = np.empty(nnz, dtype=np.int32)
+    val = np.empty(nnz, dtype=np.float64)
+    lib.synth_blockdiag(m, bmin, bmax, seed, _p(row_ptr), _p(col), _p(val))
+    return CSR(m, m, row_ptr, col, val, name="blockdiag%d" % m)
+
+
+def long_rows(m: int, nlong: int, long_len: int, seed: int) -> CSR:
+    """Short rows (lengths U{1..8}) with `nlong` seeded rows of `long_len`
+    entries; sorted distinct uniform columns in [0, m)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lens = rng.integers(1, 9, size=m).astype(np.int64)
+    lens[rng.choice(m, size=min(nlong, m), replace=False)] = min(long_len, m)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(lens, out=row_ptr[1:])
+    if row_ptr[-1] > 0x7fffffff:
+        raise MemoryError("long_rows: nnz past int32")
+    row_ptr = row_ptr.astype(np.int32)
+    nnz = int(row_ptr[-1])
+    col = np.empty(nnz, dtype=np.int32)
+    val = np.empty(nnz, dtype=np.float64)
+    _load().synth_fill_uniform(m, m, _p(row_ptr), seed, _p(col), _p(val))
+    return CSR(m, m, row_ptr, col, val, name="longrows%d" % m)
 
 
 BATCH_FAMILIES = ("banded", "uniform", "rmat")

@@ -347,3 +347,36 @@ int64_t synth_range_rows_ptr(int32_t m, int32_t lo, int32_t hi, uint64_t seed, i
     }
     return acc;
 }
+
+/* Block-diagonal with dense blocks: consecutive blocks of size drawn      */
+/* uniformly from {bmin..bmax} (the last one cut at m); every entry of a   */
+/* block is stored, values U[-1,1).  col/val may be NULL to count only.    */
+/* Returns nnz (or -1 past int32).                                        */
+int64_t synth_blockdiag(int32_t m, int32_t bmin, int32_t bmax, uint64_t seed,
+                        int32_t *row_ptr, int32_t *col, double *val)
+{
+    int64_t acc = 0;
+    int32_t r = 0;
+    uint64_t blk = 0;
+    row_ptr[0] = 0;
+    while (r < m) {
+        int32_t b = bmin + (int32_t)below(seed, ST_LEN, blk++, (uint64_t)(bmax - bmin + 1));
+        if (b > m - r) b = m - r;
+        for (int32_t i = 0; i < b; ++i) {
+            acc += b;
+            if (acc > 0x7fffffffLL) return -1;
+            row_ptr[r + i + 1] = (int32_t)acc;
+            if (col) {
+                int64_t q = acc - b;
+                for (int32_t j = 0; j < b; ++j) col[q + j] = r + j;
+            }
+        }
+        r += b;
+    }
+    if (val) {
+        #pragma omp parallel for schedule(static)
+        for (int64_t q = 0; q < acc; ++q)
+            val[q] = sym(seed, ST_VAL, (uint64_t)q);
+    }
+    return acc;
+}

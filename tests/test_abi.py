@@ -141,3 +141,20 @@ def test_plan_host_checks(lib):
     assert h.value is None
     assert L.ssspmv_plan_execute(None, FAKE, FAKE, FAKE, FAKE, None, None) == S.SSSPMV_EINVAL
     S.ssspmv_plan_destroy(None)  # a no-op
+
+
+def test_rows_variant_host_checks(lib):
+    o = S.make_opts(W=3, variant=S.VARIANT_ROWS)        # lanes per row: a power of two <= 32
+    assert S.ssspmv_csr_f64(4, 4, 8, FAKE, FAKE, FAKE, FAKE, FAKE, opts=o, workspace=FAKE,
+                            ws_bytes=1 << 30) == S.SSSPMV_EINVAL
+    o = S.make_opts(W=8, variant=S.VARIANT_ROWS)
+    assert S.ssspmv_workspace_bytes(100, 1000, 8, o) > 0
+    assert S.ssspmv_plan_shape(100, 1000, 8, o)["W"] == 8
+    # FP64 single calls only
+    assert S.ssspmv_csr_f32(4, 4, 8, FAKE, FAKE, FAKE, FAKE, FAKE, opts=o, workspace=FAKE,
+                            ws_bytes=1 << 30) == S.SSSPMV_EUNSUPPORTED
+    assert S.ssspmv_batched_workspace_bytes(3, 1000, 4, o) == 0
+    import ctypes
+    h = ctypes.c_void_p()
+    assert S._lib().ssspmv_plan_create(4, 4, 8, FAKE, 8, ctypes.byref(o), None, 0, None,
+                                       ctypes.byref(h)) == S.SSSPMV_EUNSUPPORTED
