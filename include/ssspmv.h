@@ -83,7 +83,7 @@ extern "C" {
 #define SSSPMV_VARIANT_SPECULATIVE 1
 #define SSSPMV_VARIANT_EXACT       2
 /*  ROWS         not the paper's method but the row-parallel CSR kernels it
- *               compares against (Sec. 2.2), offered as a class for the
+ *               compares against (Sec. 2.1, 4.3), offered as a class for the
  *               variant selector: a group of opts->W lanes per row (1 = the
  *               scalar kernel, 2..32 powers of two = the vector kernel; 0 =
  *               from the mean row length).  No partition and no calibration;

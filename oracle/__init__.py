@@ -9,7 +9,7 @@ through ctypes.
 Functions (each cites the passage it follows in ``oracle.c``):
 
 * ``spmv(A, x)``             plain row loop, y = A x (Sec. 2.1)
-* ``spmv_omp(A, x)``         same, rows split over OpenMP threads (Sec. 4.2)
+* ``spmv_omp(A, x)``         same, rows split over OpenMP threads (Sec. 4.3)
 * ``spmv_dot2(A, x)``        compensated reference and per-row scale
                              sum_k |a_k x_k| (Ogita-Rump-Oishi Dot2)
 * ``tile_offsets``, ``descriptors``, ``tile_flags``  index artefacts (Sec. 3.2)
@@ -92,7 +92,7 @@ def spmv(row_ptr, col, val, x) -> np.ndarray:
 
 def spmv_omp(row_ptr, col, val, x, nthreads: int = 0, y=None):
     """Row loop with rows split over OpenMP threads (the paper's CPU row-block
-    method, Sec. 4.2).  Returns (y, threads used)."""
+    method, Sec. 4.3).  Returns (y, threads used)."""
     row_ptr, col, val = _csr(row_ptr, col, val)
     x = np.ascontiguousarray(x, dtype=np.float64)
     m = len(row_ptr) - 1

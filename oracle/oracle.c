@@ -12,7 +12,7 @@
  * Contents
  *   1. The plain definition y = A x (Sec. 2.1): a row loop, serial and with
  *      rows split over OpenMP threads (the paper's CPU row-block method,
- *      Sec. 4.2), plus a compensated reference (Dot2) and the per-row scale
+ *      Sec. 4.3), plus a compensated reference (Dot2) and the per-row scale
  *      sum_k |val_k * x[col_k]| used by the tolerance.
  *   2. The index artefacts of the method, each from its definition:
  *      tile offsets (Sec. 3.2, rightmost match, by a linear merge rather than
@@ -63,7 +63,7 @@ void oracle_spmv_rowloop(int32_t m, const int32_t *row_ptr, const int32_t *col,
 }
 
 /* same loop, rows split into contiguous blocks over OpenMP threads (the CPU
- * row-block method the paper benchmarks, Sec. 4.2).  Returns threads used. */
+ * row-block method the paper benchmarks, Sec. 4.3).  Returns threads used. */
 int oracle_spmv_rowloop_omp(int32_t m, const int32_t *row_ptr, const int32_t *col,
                             const double *val, const double *x, double *y, int nthreads)
 {

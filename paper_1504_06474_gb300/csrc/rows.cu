@@ -1,8 +1,8 @@
-// rows.cu -- row-parallel CSR kernels (the baselines the paper compares its
-// method against, Sec. 2.2): a group of G lanes per row, G = 1 being the
-// scalar kernel (one thread per row) and G = 2..32 the vector kernel (the
-// lanes of a group stride over the row's entries and combine their sums with
-// shuffles).  They need no partition and no calibration, and beat the
+// rows.cu -- row-parallel CSR kernels (the CSR-scalar and CSR-vector methods
+// the paper describes in Sec. 2.1 and benchmarks against in Sec. 4.3): a
+// group of G lanes per row, G = 1 being the scalar kernel (one thread per
+// row) and G = 2..32 the vector kernel (the lanes of a group stride over the
+// row's entries and combine their sums with shuffles).  They need no partition and no calibration, and beat the
 // segmented sum where every row has about the same, small length; they are
 // classes the selector can choose.  FP64, FMA accumulation, fixed order:
 // runs are deterministic.
