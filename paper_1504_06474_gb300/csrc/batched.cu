@@ -277,7 +277,9 @@ int run_batched_shape(int32_t count, const void *desc, const BatchLayout &l, uns
         a.nblk_sync = (int32_t)((l.cap_bunches + 32 * kCalibWarps - 1) / (32 * kCalibWarps));
         a.nblk_zero = count < 4 * sms ? (count > 0 ? count : 1) : 4 * sms;
         const unsigned grid = (unsigned)(a.nblk_tiles + a.nblk_sync + a.nblk_zero);
-        calibrate_kernel<P, true><<<grid, kCalibWarps * 32, 0, stream>>>(a);
+        const size_t smem = calib_smem_bytes<P>(l.L);
+        if ((e = calib_smem_attr<P, true>(smem)) != cudaSuccess) return record_cuda_error(e);
+        calibrate_kernel<P, true><<<grid, kCalibWarps * 32, smem, stream>>>(a);
     }
     if (ev && (e = cudaEventRecord(ev[3], stream)) != cudaSuccess) return record_cuda_error(e);
     e = cudaGetLastError();

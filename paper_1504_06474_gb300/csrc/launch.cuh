@@ -76,6 +76,28 @@ int segsum_block_warps(const Call &c)
     return l1w < B ? l1w : B;
 }
 
+// kernel (c)'s shared memory: one buffer of L+1 partials per warp (the
+// repair of a dirty tile), and the attribute that allows it past 48 KB
+template <class P>
+size_t calib_smem_bytes(int32_t L)
+{
+    return (size_t)kCalibWarps * (size_t)(L + 1) * sizeof(typename P::y_t);
+}
+
+template <class P, bool BATCHED>
+cudaError_t calib_smem_attr(size_t smem)
+{
+    static size_t done[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (done[dev] >= smem) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(calibrate_kernel<P, BATCHED>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) done[dev] = smem;
+    return e;
+}
+
 // S (tiles per bunch) and the bunch count for this call
 template <class P, int W>
 void resolve_bunches(Layout &l, int32_t S_opt)
@@ -184,7 +206,9 @@ int run_shape(const Call &c)
         a.nblk_sync = (int32_t)((l.nbunches + 32 * kCalibWarps - 1) / (32 * kCalibWarps));
         a.nblk_zero = kZeroBlocks;
         const unsigned grid = (unsigned)(a.nblk_tiles + a.nblk_sync + a.nblk_zero);
-        calibrate_kernel<P><<<grid, kCalibWarps * 32, 0, c.stream>>>(a);
+        const size_t smem = calib_smem_bytes<P>(l.L);
+        if ((e = calib_smem_attr<P, false>(smem)) != cudaSuccess) return record_cuda_error(e);
+        calibrate_kernel<P><<<grid, kCalibWarps * 32, smem, c.stream>>>(a);
     }
     if (c.ev && (e = cudaEventRecord(c.ev[3], c.stream)) != cudaSuccess)
         return record_cuda_error(e);

@@ -753,15 +753,17 @@ constexpr int kCalibWarps = 8;
 // re-arrangement of one dirty tile by a warp (Sec. 3.2, checking
 // prediction): the s-th partial (s >= 1, speculatively at y[start+s]) moves to
 // the s-th non-empty row inside (start, stop), and the empty rows there become
-// 0.  Rows are walked downwards so that every slot is read before any write
-// can reach it (a partial only moves up).
+// 0.  The K partials are first copied to the warp's shared buffer `part`
+// (K <= L), so the rows can then be written in any order: the warp walks them
+// forwards, four chunks of 32 rows per round trip of row pointers.
 // t is the tile's index in its matrix and tile_offset that matrix's offsets.
 template <class P>
 __device__ __forceinline__ void repair_dirty_tile(const int32_t *__restrict__ row_ptr,
                                                   typename P::y_t *__restrict__ y,
                                                   const int32_t *__restrict__ tile_offset,
                                                   int32_t m, int32_t nnz, int32_t L, int64_t t,
-                                                  uint32_t info, uint32_t *err, int lane)
+                                                  uint32_t info, uint32_t *err, int lane,
+                                                  typename P::y_t *part)
 {
     using Y = typename P::y_t;
     const int32_t nseg = (int32_t)(info & kInfoSegMask);
@@ -771,25 +773,42 @@ __device__ __forceinline__ void repair_dirty_tile(const int32_t *__restrict__ ro
     const bool cont = stop < m && (int64_t)__ldg(row_ptr + stop) < e;
     // non-empty rows strictly inside (start, stop): each holds one segment
     const int32_t K = nseg - 1 - (cont ? 1 : 0);
-    int32_t above = 0;
-    for (int32_t hi = stop - 1; hi > start; hi -= 32) {
-        const int32_t r = hi - lane;
-        const bool valid = r > start;
-        const bool ne = valid && __ldg(row_ptr + r + 1) > __ldg(row_ptr + r);
-        const unsigned mask = __ballot_sync(FULL, ne);
-        const int32_t q = above + __popc(mask & ((1u << lane) - 1u));
-        Y v = Y(0);
-        if (ne) {
-            const int32_t sidx = K - q;
-            if (sidx >= 1 && sidx <= K) v = y[start + sidx];
-            else atomicOr(err, SSSPMV_DEV_CALIB);
-        }
-        __syncwarp();
-        if (valid) y[r] = ne ? v : Y(0);
-        above += __popc(mask);
-        __syncwarp();
+    if (K < 0 || K > L) {
+        if (lane == 0) atomicOr(err, SSSPMV_DEV_CALIB);
+        return;
     }
-    if (lane == 0 && above != K) atomicOr(err, SSSPMV_DEV_CALIB);
+    for (int32_t q = 1 + lane; q <= K; q += 32) part[q] = y[start + q];
+    __syncwarp();
+    auto rp = [&](int32_t r) { return __ldg(row_ptr + (r < m ? r : m)); };
+    int32_t before = 0;  // non-empty rows in (start, r) so far
+    for (int32_t rb = start + 1; rb < stop; rb += 128) {
+        int32_t pr[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) pr[u] = rp(rb + 32 * u + lane);
+        const int32_t tail = (lane == 31) ? rp(rb + 128) : 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int32_t r = rb + 32 * u + lane;
+            const int32_t lead = __shfl_sync(FULL, pr[u < 3 ? u + 1 : 3], 0);
+            int32_t nx = __shfl_down_sync(FULL, pr[u], 1);
+            if (lane == 31) nx = (u < 3) ? lead : tail;
+            const bool valid = r < stop;
+            const bool ne = valid && nx > pr[u];
+            const unsigned mask = __ballot_sync(FULL, ne);
+            const int32_t q = before + 1 + __popc(mask & ((1u << lane) - 1u));
+            if (valid) {
+                Y v = Y(0);
+                if (ne) {
+                    if (q <= K) v = part[q];
+                    else atomicOr(err, SSSPMV_DEV_CALIB);
+                }
+                y[r] = v;
+            }
+            before += __popc(mask);
+        }
+    }
+    if (lane == 0 && before != K) atomicOr(err, SSSPMV_DEV_CALIB);
+    __syncwarp();  // the buffer is reused for the warp's next tile
 }
 
 // the batch matrix holding global tile t: the last one whose first tile is
@@ -813,6 +832,8 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
     using A = typename P::acc_t;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
+    extern __shared__ __align__(16) unsigned char calib_smem[];
+    Y *part = reinterpret_cast<Y *>(calib_smem) + (size_t)warp * (a.L + 1);  // tile role only
     Y *__restrict__ y = static_cast<Y *>(a.y);
     const int64_t ntiles = BATCHED ? (int64_t)__ldg(a.totals) : a.ntiles;
     const int64_t nbunches = BATCHED ? (int64_t)__ldg(a.totals + 1) : a.nbunches;
@@ -832,10 +853,10 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
                 repair_dirty_tile<P>(ldg_ptr(&mm->row_ptr),
                                      static_cast<Y *>(ldg_ptr(const_cast<void *const *>(&mm->y))),
                                      a.tile_offset + tb + mi, __ldg(&mm->m), __ldg(&mm->nnz), a.L,
-                                     t - tb, info, a.err, lane);
+                                     t - tb, info, a.err, lane, part);
             } else {
                 repair_dirty_tile<P>(a.row_ptr, y, a.tile_offset, a.m, a.nnz, a.L, t, info, a.err,
-                                     lane);
+                                     lane, part);
             }
         }
         return;

@@ -305,6 +305,18 @@ def load(path: str) -> np.ndarray:
     return np.asarray(d["params"], np.float32)
 
 
+DEFAULT_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_weights.json")
+
+
+def load_default():
+    """The weights trained by this module's command line on 2,000 generated
+    matrices (shipped with the package), or None if absent."""
+    try:
+        return load(DEFAULT_WEIGHTS)
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def choose_opts(rp, m: int, n: int, nnz: int, params=None, timer=None):
     """opts for ssspmv_csr_f64 on this matrix: the selector's class, or the
     defaults when there is no model."""

@@ -16,6 +16,7 @@ by synthetic matrices because the real collection is not available):
   109,215,352 nnz), diagonal 26.0, off-diagonals -1.0 + U[-0.01, 0.01),
   x ~ U[-1, 1), seed 1.
 * ``stencil<k>``   the same stencil on a k^3 grid (smaller cases for profiling).
+* ``rmat<k>``      the R-MAT recipe below at scale k, injected row 10^6 * 2^(k-22).
 * ``rmat22``       R-MAT scale 22, edge factor 16, (0.57, 0.19, 0.19, 0.05),
   duplicates merged, self loops kept, one seeded row replaced by 1,000,000
   distinct uniform sorted columns, val and x ~ U[-1, 1), seed 2.
@@ -265,6 +266,11 @@ def workload(name: str) -> tuple[CSR, np.ndarray]:
     if name == "rmat22":
         A = rmat(22, 16, (0.57, 0.19, 0.19), seed=2, inject_len=1_000_000)
         A.name = "rmat22"
+        return A, sym_vector(A.n, seed=2)
+    if name.startswith("rmat") and name[4:].isdigit():
+        k = int(name[4:])          # the same recipe at scale k (the injected row scaled with m)
+        A = rmat(k, 16, (0.57, 0.19, 0.19), seed=2, inject_len=(1_000_000 << k) >> 22)
+        A.name = name
         return A, sym_vector(A.n, seed=2)
     raise KeyError(name)
 
