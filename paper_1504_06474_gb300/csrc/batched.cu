@@ -274,6 +274,7 @@ int run_batched_shape(int32_t count, const void *desc, const BatchLayout &l, uns
         int64_t tblk = (l.cap_tiles + kCalibWarps - 1) / kCalibWarps;
         const int64_t tcap = (int64_t)sms * 16;
         a.nblk_tiles = (int32_t)(tblk < tcap ? (tblk > 0 ? tblk : 1) : tcap);
+        a.span = calib_span(l.cap_tiles, a.nblk_tiles);
         a.nblk_sync = (int32_t)((l.cap_bunches + 32 * kCalibWarps - 1) / (32 * kCalibWarps));
         a.nblk_zero = count < 4 * sms ? (count > 0 ? count : 1) : 4 * sms;
         const unsigned grid = (unsigned)(a.nblk_tiles + a.nblk_sync + a.nblk_zero);

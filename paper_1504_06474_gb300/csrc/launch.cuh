@@ -76,6 +76,15 @@ int segsum_block_warps(const Call &c)
     return l1w < B ? l1w : B;
 }
 
+// tiles per warp window of kernel (c)'s tile role: the tiles spread evenly
+// over its warps, read in one round of loads (at most 32 per window)
+inline int32_t calib_span(int64_t ntiles, int32_t nblk_tiles)
+{
+    const int64_t nw = (int64_t)(nblk_tiles > 0 ? nblk_tiles : 1) * kCalibWarps;
+    int64_t s = (ntiles + nw - 1) / nw;
+    return (int32_t)(s < 1 ? 1 : (s > 32 ? 32 : s));
+}
+
 // kernel (c)'s shared memory: one buffer of L+1 partials per warp (the
 // repair of a dirty tile), and the attribute that allows it past 48 KB
 template <class P>
@@ -203,6 +212,7 @@ int run_shape(const Call &c)
         int64_t tblk = (l.ntiles + kCalibWarps - 1) / kCalibWarps;
         const int64_t tcap = (int64_t)device_sm_count() * 16;
         a.nblk_tiles = (int32_t)(tblk < tcap ? tblk : tcap);
+        a.span = calib_span(l.ntiles, a.nblk_tiles);
         a.nblk_sync = (int32_t)((l.nbunches + 32 * kCalibWarps - 1) / (32 * kCalibWarps));
         a.nblk_zero = kZeroBlocks;
         const unsigned grid = (unsigned)(a.nblk_tiles + a.nblk_sync + a.nblk_zero);

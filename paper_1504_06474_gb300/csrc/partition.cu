@@ -99,7 +99,7 @@ void launch_partition(const int32_t *row_ptr, int32_t m, int32_t nnz, int32_t L,
 {
     if (method == 1) {
         int64_t blocks = ((int64_t)m + 4 * kPartitionThreads - 1) / (4 * kPartitionThreads);
-        const int64_t cap = 8LL * device_sm_count();
+        const int64_t cap = 32LL * device_sm_count();  // one pass: more rows in flight
         if (blocks > cap) blocks = cap;
         if (blocks < 1) blocks = 1;
         switch (L / 32) {

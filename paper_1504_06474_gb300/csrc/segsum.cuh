@@ -741,6 +741,7 @@ struct CalibArgs {
     int32_t nblk_tiles;
     int32_t nblk_sync;
     int32_t nblk_zero;
+    int32_t span;  // tiles per warp window of the tile role (1..32)
     // batches only (see SegsumArgs)
     const BatchMat *mats = nullptr;
     const int32_t *bunch_mat = nullptr;
@@ -842,10 +843,20 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
     if (blk < a.nblk_tiles) {
         // ---- re-arrangement of dirty tiles (Sec. 3.2, checking prediction):
         // the warps of this role stride over the tiles
+        // (warp w takes tiles w, w + nw, w + 2 nw, ...: dirty tiles cluster,
+        // so striding spreads them over the warps; `span` of them are read in
+        // one round of loads, then the dirty ones are repaired in turn)
         const int64_t nw = (int64_t)a.nblk_tiles * kCalibWarps;
-        for (int64_t t = (int64_t)blk * kCalibWarps + warp; t < ntiles; t += nw) {
-            const uint32_t info = __ldg(a.tile_info + t);
-            if (!(info & kInfoDirty) || (info & kInfoResolved)) continue;
+        const int64_t span = a.span;
+        for (int64_t t0 = (int64_t)blk * kCalibWarps + warp; t0 < ntiles; t0 += nw * span) {
+            const int64_t tl = t0 + (int64_t)lane * nw;
+            const uint32_t il = (lane < span && tl < ntiles) ? __ldg(a.tile_info + tl) : 0u;
+            unsigned todo = __ballot_sync(FULL, (il & kInfoDirty) && !(il & kInfoResolved));
+            while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t t = t0 + (int64_t)src * nw;
+            const uint32_t info = __shfl_sync(FULL, il, src);
             if constexpr (BATCHED) {
                 const int32_t mi = batch_matrix_of_tile(a.mats, a.count, t);
                 const BatchMat *mm = a.mats + mi;
@@ -857,6 +868,7 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
             } else {
                 repair_dirty_tile<P>(a.row_ptr, y, a.tile_offset, a.m, a.nnz, a.L, t, info, a.err,
                                      lane, part);
+            }
             }
         }
         return;
