@@ -164,6 +164,19 @@ int ssspmv_csr_bf16f32(int32_t m, int32_t n, int32_t nnz,
                        const float *x, float *y,
                        const ssspmv_opts *opts, void *workspace, size_t ws_bytes, void *stream);
 
+/* y = alpha A x + beta y in FP64 (the iterative-solver form; the paper computes
+ * y = A x only).  Same arguments and contract as ssspmv_csr_f64 plus the two
+ * scalars; y is read only where beta != 0 (so with beta == 0 it may hold
+ * anything, NaN included).  The partials of tiles with empty rows are always
+ * stored at their true rows (SSSPMV_VARIANT_EXACT, whatever opts->variant
+ * says, except SSSPMV_VARIANT_ROWS), because a speculative store would
+ * overwrite a row of y before its old value is read.  Each row's result is
+ * fma(beta, y_old, alpha * (A x)_row). */
+int ssspmv_csr_f64_axpby(int32_t m, int32_t n, int32_t nnz,
+                         const int32_t *row_ptr, const int32_t *col_idx, const double *val,
+                         const double *x, double *y, double alpha, double beta,
+                         const ssspmv_opts *opts, void *workspace, size_t ws_bytes, void *stream);
+
 /* The library-owned workspace of the current device and `stream` (the one
  * calls with workspace == NULL use), e.g. for ssspmv_device_status.  Returns
  * SSSPMV_EWORKSPACE (and NULL, 0) if no call on that stream has made one yet.
@@ -198,6 +211,11 @@ int ssspmv_plan_create(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr
 int ssspmv_plan_execute(ssspmv_plan *plan, const int32_t *col_idx, const void *val,
                         const void *x, void *y, void *timer, void *stream);
 int ssspmv_plan_workspace(const ssspmv_plan *plan, void **ptr, size_t *bytes);
+/* y = alpha A x + beta y with the plan's partition (FP64 plans only, else
+ * SSSPMV_EUNSUPPORTED); exact stores, as for ssspmv_csr_f64_axpby. */
+int ssspmv_plan_execute_axpby(ssspmv_plan *plan, const int32_t *col_idx, const void *val,
+                              const void *x, void *y, double alpha, double beta, void *timer,
+                              void *stream);
 void ssspmv_plan_destroy(ssspmv_plan *plan);
 
 /* Batched FP32 products y_i = A_i x_i for `count` matrices of any sizes in

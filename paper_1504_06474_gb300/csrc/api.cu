@@ -219,7 +219,8 @@ static int cached_workspace(size_t need, void *stream, void **ptr, size_t *bytes
 static int run_call(int32_t val_bytes, int32_t m, int32_t n, int32_t nnz,
                     const int32_t *row_ptr, const int32_t *col, const void *val, const void *x,
                     void *y, const ssspmv_opts *opts, void *ws, size_t ws_bytes, void *stream,
-                    uint32_t *dbg_desc, void *dbg_yspec, Layout *out_layout)
+                    uint32_t *dbg_desc, void *dbg_yspec, Layout *out_layout,
+                    double alpha = 1.0, double beta = 0.0, int axpby = 0)
 {
     const Prec *pr = prec_for(val_bytes);
     if (!pr) return SSSPMV_EUNSUPPORTED;
@@ -250,6 +251,9 @@ static int run_call(int32_t val_bytes, int32_t m, int32_t n, int32_t nnz,
         c.ws = static_cast<unsigned char *>(ws);
         c.stream = static_cast<cudaStream_t>(stream);
         c.ev = opts->timer ? timer_next_slot(static_cast<ssspmv_timer *>(opts->timer)) : nullptr;
+        c.alpha = alpha;
+        c.beta = beta;
+        c.axpby = axpby;
         return run_rows_f64(c, l.W);
     }
     rc = pr->resolve(l, opts ? opts->S : 0);
@@ -274,6 +278,14 @@ static int run_call(int32_t val_bytes, int32_t m, int32_t n, int32_t nnz,
     c.dbg_yspec = dbg_yspec;
     c.exact = (opts && opts->variant == SSSPMV_VARIANT_EXACT) ? 1 : 0;
     c.block_warps = opts ? opts->block_warps : 0;
+    if (axpby) {
+        // speculative stores would overwrite y before its old values are
+        // read: scaled products always store exactly
+        c.exact = 1;
+        c.alpha = alpha;
+        c.beta = beta;
+        c.axpby = 1;
+    }
     return pr->run(c);
 }
 
@@ -650,6 +662,51 @@ void ssspmv_release_workspaces(void)
     }
     cudaSetDevice(cur);
     g_ws.clear();
+}
+
+int ssspmv_csr_f64_axpby(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr,
+                         const int32_t *col_idx, const double *val, const double *x, double *y,
+                         double alpha, double beta, const ssspmv_opts *opts, void *workspace,
+                         size_t ws_bytes, void *stream)
+{
+    return run_call(8, m, n, nnz, row_ptr, col_idx, val, x, y, opts, workspace, ws_bytes, stream,
+                    nullptr, nullptr, nullptr, alpha, beta, 1);
+}
+
+int ssspmv_plan_execute_axpby(ssspmv_plan *p, const int32_t *col_idx, const void *val,
+                              const void *x, void *y, double alpha, double beta, void *timer,
+                              void *stream)
+{
+    if (!p) return SSSPMV_EINVAL;
+    if (p->val_bytes != 8) return SSSPMV_EUNSUPPORTED;
+    const Prec *pr = prec_for(p->val_bytes);
+    int rc = check_csr_args(p->m, p->n, p->nnz, p->row_ptr, col_idx, val, x, y);
+    if (rc) return rc;
+    if (p->m == 0) return SSSPMV_OK;
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return record_cuda_error(e);
+    if (dev != p->dev) return SSSPMV_EINVAL;
+    Call c;
+    c.m = p->m;
+    c.n = p->n;
+    c.nnz = p->nnz;
+    c.row_ptr = p->row_ptr;
+    c.col = col_idx;
+    c.val = val;
+    c.x = x;
+    c.y = y;
+    c.lay = p->lay;
+    c.ws = static_cast<unsigned char *>(p->ws);
+    c.stream = static_cast<cudaStream_t>(stream);
+    c.ev = timer ? timer_next_slot(static_cast<ssspmv_timer *>(timer)) : nullptr;
+    c.exact = 1;  // see run_call
+    c.block_warps = p->block_warps;
+    c.skip_partition = 1;
+    c.alpha = alpha;
+    c.beta = beta;
+    c.axpby = 1;
+    return pr->run(c);
 }
 
 int ssspmv_csr_f64_debug(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr,

@@ -21,6 +21,8 @@ struct Call {
     int exact = 0;                   // dirty tiles store in their true rows
     int block_warps = 0;             // warps per block of kernel (b); 0: the most that fit
     int skip_partition = 0;          // plan execution: tile offsets already in the workspace
+    double alpha = 1.0, beta = 0.0;  // y = alpha A x + beta y when axpby (exact stores)
+    int axpby = 0;
     uint32_t *dbg_desc = nullptr;    // ntiles*W words or null
     void *dbg_yspec = nullptr;       // m values or null
 };
@@ -166,6 +168,9 @@ int run_shape(const Call &c)
         a.ntiles = l.ntiles;
         a.nbunches = l.nbunches;
         a.S = l.S;
+        a.alpha = c.alpha;
+        a.beta = c.beta;
+        a.axpby = c.axpby;
         auto kb = c.exact ? segsum_kernel<P, W, B, BS.blocks, true>
                           : segsum_kernel<P, W, B, BS.blocks, false>;
         static int attr_done[2][64] = {{0}};
@@ -213,6 +218,9 @@ int run_shape(const Call &c)
         const int64_t tcap = (int64_t)device_sm_count() * 16;
         a.nblk_tiles = (int32_t)(tblk < tcap ? tblk : tcap);
         a.span = calib_span(l.ntiles, a.nblk_tiles);
+        a.alpha = c.alpha;
+        a.beta = c.beta;
+        a.axpby = c.axpby;
         a.nblk_sync = (int32_t)((l.nbunches + 32 * kCalibWarps - 1) / (32 * kCalibWarps));
         a.nblk_zero = kZeroBlocks;
         const unsigned grid = (unsigned)(a.nblk_tiles + a.nblk_sync + a.nblk_zero);

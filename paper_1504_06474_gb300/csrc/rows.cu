@@ -18,7 +18,7 @@ template <int G>
 __global__ void __launch_bounds__(kRowThreads)
     csr_rows_kernel(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                     const double *__restrict__ val, const double *__restrict__ x,
-                    double *__restrict__ y, int32_t m)
+                    double *__restrict__ y, int32_t m, double alpha, double beta, int32_t axpby)
 {
     static_assert(G >= 1 && G <= 32 && (G & (G - 1)) == 0, "G is a power of two up to 32");
     constexpr int RPW = 32 / G;  // rows per warp per pass
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(kRowThreads)
         double s = s0 + s1;
 #pragma unroll
         for (int d = G / 2; d >= 1; d >>= 1) s += __shfl_xor_sync(FULL, s, d);
-        if (r < m && sub == 0) y[r] = s;
+        if (r < m && sub == 0) y[r] = scaled_store_value(y, r, s, alpha, beta, axpby);
     }
 }
 
@@ -77,7 +77,8 @@ int run_rows_f64(const Call &c, int group)
         switch (g) {
 #define X(G)                                                                                   \
     case G:                                                                                    \
-        csr_rows_kernel<G><<<grid, kRowThreads, 0, c.stream>>>(c.row_ptr, c.col, val, x, y, c.m); \
+        csr_rows_kernel<G><<<grid, kRowThreads, 0, c.stream>>>(c.row_ptr, c.col, val, x, y, c.m, \
+                                                               c.alpha, c.beta, c.axpby);      \
         break;
             X(1) X(2) X(4) X(8) X(16) X(32)
 #undef X

@@ -217,7 +217,21 @@ struct SegsumArgs {
     const BatchMat *mats = nullptr;
     const int32_t *bunch_mat = nullptr;
     const int32_t *totals = nullptr;
+    // y = alpha A x + beta y (exact stores only; off: y = A x)
+    double alpha = 1.0, beta = 0.0;
+    int32_t axpby = 0;
 };
+
+// the value a final store of row `row` writes: v, or alpha v + beta y[row]
+// (y is not read when beta is 0)
+template <class Y>
+__device__ __forceinline__ Y scaled_store_value(const Y *y, int64_t row, Y v, double alpha,
+                                                double beta, int32_t on)
+{
+    if (!on) return v;
+    const double av = alpha * (double)v;
+    return (Y)(beta != 0.0 ? fma(beta, (double)y[row], av) : av);
+}
 
 // tile_info layout: bit 31 dirty, bit 30 dirty and resolved by kernel (b),
 // bits 0..29 number of segments
@@ -235,7 +249,8 @@ constexpr uint32_t kInfoSegMask = 0x3fffffffu;
 template <bool EXACT, class Y>
 __device__ __noinline__ uint32_t scan_rows_long(const int32_t *__restrict__ row_ptr, int32_t m,
                                                 int32_t rb0, int32_t stop, int32_t b, int32_t len,
-                                                uint32_t *desc, int32_t *rowmap, Y *y)
+                                                uint32_t *desc, int32_t *rowmap, Y *y,
+                                                double alpha, double beta, int32_t axpby)
 {
     constexpr int CH = 4;
     const int lane = threadIdx.x & 31;
@@ -263,7 +278,7 @@ __device__ __noinline__ uint32_t scan_rows_long(const int32_t *__restrict__ row_
                 if (r < stop) {
                     if (nx == pr) {
                         flags |= 1u;
-                        if (EXACT) y[r] = Y(0);
+                        if (EXACT) y[r] = scaled_store_value(y, r, Y(0), alpha, beta, axpby);
                     } else if (EXACT && k > 0) {
                         rowmap[k] = r;
                     }
@@ -543,7 +558,8 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
                 if (r < stop) {
                     if (nx == pr) {
                         dirty = true;
-                        if (EXACT) y[r] = Y(0);  // r > start: row `start` is never empty
+                        // r > start: row `start` is never empty
+                        if (EXACT) y[r] = scaled_store_value(y, r, Y(0), a.alpha, a.beta, a.axpby);
                     } else if (EXACT && k > 0) {
                         rowmap[k] = (int32_t)r;
                     }
@@ -564,7 +580,8 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
                 scan_row(start + 32 + lane, pr_chunk2, nx);
                 if (start + 64 <= stop) {  // long row ranges
                     const uint32_t f = scan_rows_long<EXACT, Y>(row_ptr, mrows, start + 64, stop,
-                                                                b, len, desc, rowmap, y);
+                                                                b, len, desc, rowmap, y, a.alpha,
+                                                                a.beta, a.axpby);
                     dirty |= (f & 1u) != 0;
                     cont |= (f & 2u) != 0;
                 }
@@ -598,7 +615,12 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
                 } else {
                     int32_t row = start + sidx;
                     if (EXACT && resolve) row = hpos <= 0 ? start : rowmap[hpos < L ? hpos : 0];
-                    if (row >= 0 && row < mrows) y[row] = P::out(v);
+                    if (row >= 0 && row < mrows) {
+                        if constexpr (EXACT)
+                            y[row] = scaled_store_value(y, row, P::out(v), a.alpha, a.beta, a.axpby);
+                        else
+                            y[row] = P::out(v);
+                    }
                     else atomicOr(a.err, SSSPMV_DEV_RANGE);
                 }
             };
@@ -742,6 +764,8 @@ struct CalibArgs {
     int32_t nblk_sync;
     int32_t nblk_zero;
     int32_t span;  // tiles per warp window of the tile role (1..32)
+    double alpha = 1.0, beta = 0.0;  // y = alpha A x + beta y (see SegsumArgs)
+    int32_t axpby = 0;
     // batches only (see SegsumArgs)
     const BatchMat *mats = nullptr;
     const int32_t *bunch_mat = nullptr;
@@ -931,7 +955,7 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
             const int64_t wl = base + first;  // the run's leader
             double total = C;
             if (wl > 0 && __ldg(a.tail_flag + wl - 1)) total += tv[wl - 1];
-            if (r >= 0 && r < mw) yw[r] = (Y)total;
+            if (r >= 0 && r < mw) yw[r] = scaled_store_value(yw, r, (Y)total, a.alpha, a.beta, a.axpby);
             else atomicOr(a.err, SSSPMV_DEV_RANGE);
         }
         const bool open = __shfl_sync(FULL, owned && next_same, 31);
@@ -955,7 +979,8 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
             if (lane == 0) {
                 double total = csum + acc;
                 if (wl > 0 && __ldg(a.tail_flag + wl - 1)) total += tv[wl - 1];
-                if (rr >= 0 && rr < mr) yr[rr] = (Y)total;
+                if (rr >= 0 && rr < mr)
+                    yr[rr] = scaled_store_value(yr, rr, (Y)total, a.alpha, a.beta, a.axpby);
                 else atomicOr(a.err, SSSPMV_DEV_RANGE);
             }
         }
@@ -969,13 +994,14 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
             const BatchMat *mm = a.mats + mi;
             const int32_t r0 = __ldg(a.tile_offset + __ldg(&mm->tile_base) + mi);
             Y *__restrict__ ym = static_cast<Y *>(ldg_ptr(const_cast<void *const *>(&mm->y)));
-            for (int32_t r = threadIdx.x; r < r0; r += blockDim.x) ym[r] = Y(0);
+            for (int32_t r = threadIdx.x; r < r0; r += blockDim.x)
+                ym[r] = scaled_store_value(ym, r, Y(0), a.alpha, a.beta, a.axpby);
         }
     } else {
         const int32_t r0 = __ldg(a.tile_offset);
         for (int64_t r = (int64_t)blk * blockDim.x + threadIdx.x; r < r0;
              r += (int64_t)a.nblk_zero * blockDim.x)
-            y[r] = Y(0);
+            y[r] = scaled_store_value(y, r, Y(0), a.alpha, a.beta, a.axpby);
     }
 }
 

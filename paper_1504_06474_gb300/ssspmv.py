@@ -73,6 +73,10 @@ _SIGS = {
     "ssspmv_plan_execute": (ctypes.c_int, [P, P, P, P, P, P, P]),
     "ssspmv_plan_workspace": (ctypes.c_int, [P, P, P]),
     "ssspmv_plan_destroy": (None, [P]),
+    "ssspmv_csr_f64_axpby": (ctypes.c_int, [i32, i32, i32, P, P, P, P, P, ctypes.c_double,
+                                            ctypes.c_double, OPTS, P, sz, P]),
+    "ssspmv_plan_execute_axpby": (ctypes.c_int, [P, P, P, P, P, ctypes.c_double,
+                                                 ctypes.c_double, P, P]),
     "ssspmv_batched_workspace_bytes": (sz, [i32, i64, i32, OPTS]),
     "ssspmv_features_scratch_bytes": (sz, []),
     "ssspmv_features": (ctypes.c_int, [i32, i32, i32, P, P, P, P]),
@@ -314,6 +318,21 @@ def ssspmv_plan_workspace(plan):
     check(_lib().ssspmv_plan_workspace(plan, ctypes.byref(p), ctypes.byref(b)),
           "ssspmv_plan_workspace")
     return p.value, b.value
+
+
+def ssspmv_csr_f64_axpby(m, n, nnz, row_ptr, col_idx, val, x, y, alpha, beta, opts=None,
+                         workspace=None, ws_bytes=None, stream=None) -> int:
+    if ws_bytes is None:
+        ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    return _lib().ssspmv_csr_f64_axpby(m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(val),
+                                       _ptr(x), _ptr(y), alpha, beta, _opts(opts),
+                                       _ptr(workspace), ws_bytes, _stream(stream))
+
+
+def ssspmv_plan_execute_axpby(plan, col_idx, val, x, y, alpha, beta, timer=None,
+                              stream=None) -> int:
+    return _lib().ssspmv_plan_execute_axpby(plan, _ptr(col_idx), _ptr(val), _ptr(x), _ptr(y),
+                                            alpha, beta, timer, _stream(stream))
 
 
 def ssspmv_plan_destroy(plan) -> None:
