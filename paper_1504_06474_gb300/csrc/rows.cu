@@ -61,6 +61,10 @@ int run_rows_f64(const Call &c, int group)
     cudaError_t e = cudaSuccess;
     if (c.ev && (e = cudaEventRecord(c.ev[0], c.stream)) != cudaSuccess)
         return record_cuda_error(e);
+    // the workspace's error word starts at zero, as after kernel (a)
+    if (c.ws && (e = cudaMemsetAsync(c.ws + c.lay.off_err, 0, 2 * sizeof(uint32_t), c.stream)) !=
+                    cudaSuccess)
+        return record_cuda_error(e);
     if (c.ev && (e = cudaEventRecord(c.ev[1], c.stream)) != cudaSuccess)
         return record_cuda_error(e);
     if (c.m > 0) {
