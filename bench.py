@@ -568,6 +568,15 @@ def run_batch(args):
     total_nnz = sum(A.nnz for A, _ in mats)
     f32_bytes = lambda A: algorithmic_bytes(A.m, A.n, A.nnz, val_bytes=4, y_bytes=4, x_bytes=4)
     nbytes = sum(f32_bytes(A) for A, _ in mats)
+    # tile shape and store variant chosen by the library's autotuner on this
+    # batch (unless given on the command line)
+    tuned = None
+    if args.tile_w == 0 and args.variant == 0:
+        from paper_1504_06474_gb300 import selector as S
+        torch.cuda.synchronize(dev)
+        kw, cand_ms = S.tune_batched(count, desc, total_nnz, dev)
+        tuned = {"chosen": kw, "candidates_ms": {k: round(v, 4) for k, v in cand_ms.items()}}
+        args.tile_w, args.variant = kw["W"], kw["variant"]
     opts = C.make_opts(W=args.tile_w, S=args.tile_s, variant=args.variant)
     ws = torch.empty(C.ssspmv_batched_workspace_bytes(count, total_nnz, 4, opts),
                      dtype=torch.uint8, device=dev)
@@ -672,6 +681,8 @@ def run_batch(args):
                    "rows": sum(A.m for A, _ in mats), "nnz": total_nnz,
                    "bytes_per_step": nbytes, "hbm_frac": round(value / hbm, 4),
                    "W": C.ssspmv_plan_shape(1, 1, 4, opts)["W"],
+                   "variant": ["default", "speculative", "exact"][args.variant],
+                   "autotuned": tuned,
                    "launch": "one CUDA graph replay: set-up, partition, one persistent "
                              "segmented-sum launch over every bunch of every matrix, calibration",
                    "stage_ms": stage, "separate_f32_calls_ms": round(ms_sep, 4),

@@ -184,7 +184,7 @@ int run_batched_shape(int32_t count, const void *desc, const BatchLayout &l, uns
                       cudaStream_t stream, int exact, int block_warps, cudaEvent_t *ev)
 {
     using SM = WarpSmem<P, W>;
-    constexpr BlockShape BS = pick_block_shape(SM::BYTES, P::kMaxWarps);
+    constexpr BlockShape BS = pick_block_shape(SM::BYTES, P::kBatchMaxWarps);
     constexpr int B = BS.B;
     uint32_t *err = reinterpret_cast<uint32_t *>(ws + l.off_err);
     int32_t *totals = reinterpret_cast<int32_t *>(ws + l.off_err + 8);

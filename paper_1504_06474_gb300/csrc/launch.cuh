@@ -63,8 +63,10 @@ int segsum_resident_warps(int bw)
 // shared memory for long rows; for short rows (mean below 20 entries, where
 // power-law column patterns reuse x heavily) only as many as keep the
 // shared-memory carve-out at or below 200 KB, so about 56 KB of L1 stays
-// for the gathers.  Measured on W = 15: a 27-point stencil runs 3% faster
-// with all 19 warps, an R-MAT graph 30% faster with 17.
+// for the gathers, and at most the precision's kShortRowWarps.  Measured on
+// W = 15: a 27-point stencil runs 3% faster with all 19 FP64 warps (6% with
+// 24 FP32 warps), an R-MAT graph 30% faster with 17 FP64 warps (10% with 20
+// FP32 warps).
 template <class P, int W>
 int segsum_block_warps(const Call &c)
 {
@@ -74,6 +76,7 @@ int segsum_block_warps(const Call &c)
     if (c.block_warps >= 1) return c.block_warps < B ? c.block_warps : B;
     if ((int64_t)c.nnz >= 20 * (int64_t)c.m) return B;
     int l1w = (200 * 1024 - 1024) / SM::BYTES;
+    if (l1w > P::kShortRowWarps) l1w = P::kShortRowWarps;
     if (l1w < 1) l1w = 1;
     return l1w < B ? l1w : B;
 }

@@ -31,6 +31,7 @@ namespace ssspmv {
 
 struct F64 {
     static constexpr int kMaxWarps = 32;  // shared memory decides
+    static constexpr int kShortRowWarps = 17;  // short rows: keep L1 for the gathers (measured)
     using val_t = double;
     using x_t = double;
     using y_t = double;
@@ -82,7 +83,11 @@ __device__ __forceinline__ CompF32 comp_fma(float v, float x, CompF32 a)
 
 template <class V>
 struct CompF32Traits {
-    static constexpr int kMaxWarps = 20;  // 96 registers per thread
+    // FP32 values: 24 warps (85 registers per thread, no spills at W = 15);
+    // BF16 values need more registers for the widening: 20 (96)
+    static constexpr int kMaxWarps = std::is_same<V, float>::value ? 24 : 20;
+    static constexpr int kBatchMaxWarps = 20;  // the batched kernel needs more registers
+    static constexpr int kShortRowWarps = 20;  // short rows: keep L1 for the gathers (measured)
     using val_t = V;
     using x_t = float;
     using y_t = float;

@@ -142,6 +142,33 @@ def autotune(Ad: DeviceMatrix, timer: Timer, reps: int = 3) -> np.ndarray:
     return times
 
 
+def tune_batched(count: int, desc, total_nnz: int, dev, reps: int = 3):
+    """The autotuner for a batch (ssspmv_csr_batched_f32): times every
+    compiled tile shape with speculative and exact stores on this batch and
+    returns (opts fields of the fastest, {name: ms})."""
+    import torch
+    timer = Timer(dev)
+    cands = {}
+    for W in C.ssspmv_supported_w():
+        for variant in (C.VARIANT_SPECULATIVE, C.VARIANT_EXACT):
+            cands["W%d %s" % (W, "exact" if variant == C.VARIANT_EXACT else "speculative")] = \
+                dict(W=W, variant=variant)
+    need = max(C.ssspmv_batched_workspace_bytes(count, total_nnz, 4, C.make_opts(**kw))
+               for kw in cands.values())
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    times = {}
+    for name, kw in cands.items():
+        o = C.make_opts(**kw)
+
+        def call():
+            C.check(C.ssspmv_csr_batched_f32(count, desc, total_nnz, opts=o, workspace=ws),
+                    "ssspmv_csr_batched_f32")
+        call()
+        times[name] = timer.time_ms(call, reps)
+    best = min(times, key=times.get)
+    return cands[best], times
+
+
 # ---------------------------------------------------------------------------
 # the seeded training set: six families, m log-uniform
 
