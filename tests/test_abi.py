@@ -4,6 +4,7 @@ GPU.  No kernel is launched here."""
 import ctypes
 import shutil
 
+import numpy as np
 import pytest
 
 from paper_1504_06474_gb300 import _build
@@ -158,3 +159,42 @@ def test_rows_variant_host_checks(lib):
     h = ctypes.c_void_p()
     assert S._lib().ssspmv_plan_create(4, 4, 8, FAKE, 8, ctypes.byref(o), None, 0, None,
                                        ctypes.byref(h)) == S.SSSPMV_EUNSUPPORTED
+
+
+def test_batched_and_axpby_host_checks(lib):
+    # batches: bad counts and bounds, missing or misaligned descriptor array, workspace
+    assert S.ssspmv_batched_workspace_bytes(-1, 100, 4, None) == 0
+    assert S.ssspmv_batched_workspace_bytes(3, -5, 4, None) == 0
+    assert S.ssspmv_batched_workspace_bytes(3, 100, 8, None) == 0        # FP32 only
+    need = S.ssspmv_batched_workspace_bytes(3, 1000, 4, None)
+    assert need > 0
+    L = S._lib()
+    assert L.ssspmv_csr_batched_f32(0, None, 0, None, None, 0, None) == S.SSSPMV_OK  # nothing
+    assert L.ssspmv_csr_batched_f32(3, None, 1000, None, FAKE, need, None) == S.SSSPMV_EINVAL
+    assert L.ssspmv_csr_batched_f32(3, FAKE + 4, 1000, None, FAKE, need, None) == S.SSSPMV_EINVAL
+    assert L.ssspmv_csr_batched_f32(3, FAKE, 1000, None, FAKE, need - 1, None) == S.SSSPMV_EWORKSPACE
+    assert L.ssspmv_csr_batched_f32(3, FAKE, 1000, None, FAKE + 16, need, None) == S.SSSPMV_EWORKSPACE
+    # y = alpha A x + beta y: the same argument checks as the plain call
+    assert S.ssspmv_csr_f64_axpby(-1, 4, 8, FAKE, FAKE, FAKE, FAKE, FAKE, 1.0, 0.0, workspace=FAKE,
+                                  ws_bytes=1 << 30) == S.SSSPMV_EINVAL
+    assert S.ssspmv_csr_f64_axpby(4, 4, 8, FAKE, FAKE, FAKE + 8, FAKE, FAKE, 1.0, 0.0,
+                                  workspace=FAKE, ws_bytes=1 << 30) == S.SSSPMV_EINVAL
+    assert L.ssspmv_plan_execute_axpby(None, FAKE, FAKE, FAKE, FAKE, 1.0, 0.0, None, None) == \
+        S.SSSPMV_EINVAL
+
+
+def test_selector_host_side(lib):
+    from paper_1504_06474_gb300 import selector as sel
+    assert sel.K == len(sel.CLASSES) and sel.CLASSES[0][1] == {}          # class 0: defaults
+    assert S.ssspmv_mlp_param_count(16, 64, 64, sel.K) == \
+        16 * 64 + 64 + 64 * 64 + 64 + sel.K * 64 + sel.K
+    assert S.ssspmv_mlp_param_count(0, 64, 64, 10) == 0
+    p = sel.load_default()                                                  # shipped weights
+    assert p is not None and p.size == S.ssspmv_mlp_param_count(16, 64, 64, sel.K)
+    t = np.array([[2.0, 1.0, 3.0], [1.0, 1.0, 1.0]])
+    r = sel.evaluate(np.array([1, 2]), t)
+    assert r["mean_regret"] == 0.0 and r["optimum_hit_rate"] == 1.0
+    assert np.isclose(r["geomean_speedup_vs_default"], np.sqrt(2.0))
+    specs = sel.dataset_specs(50, seed=9)
+    assert specs == sel.dataset_specs(50, seed=9)
+    assert {sp[0] for sp in specs} <= set(sel.FAMILIES)
