@@ -97,7 +97,8 @@ typedef struct ssspmv_opts {
     int32_t W;         /* entries per lane (odd, see ssspmv_supported_w); L = 32*W.
                           0 = the shortest compiled tile.  With SSSPMV_VARIANT_ROWS:
                           lanes per row (see there) */
-    int32_t S;         /* tiles per thread-bunch (warp); 0 = 4.  Each warp of a
+    int32_t S;         /* tiles per thread-bunch (warp); 0 = 4, or fewer for matrices of
+                          under 12,288 tiles (ceil(ntiles / 4096)).  Each warp of a
                           persistent grid first takes an even contiguous share of
                           3/4 of the bunches, then single bunches from a counter */
     int32_t block_warps; /* warps per block of the segmented-sum kernel (one block

@@ -128,7 +128,7 @@ static int make_layout(int32_t m, int32_t nnz, int32_t val_bytes, const ssspmv_o
     l.W = W;
     l.L = 32 * W;
     l.ntiles = ((int64_t)nnz + l.L - 1) / l.L;
-    const int32_t S = (o && o->S > 0) ? o->S : kDefaultS;
+    const int32_t S = (o && o->S > 0) ? o->S : auto_bunch_tiles(l.ntiles);
     l.nbunch_cap = (l.ntiles + S - 1) / S;
     carve(l);
     return SSSPMV_OK;

@@ -116,7 +116,7 @@ cudaError_t calib_smem_attr(size_t smem)
 template <class P, int W>
 void resolve_bunches(Layout &l, int32_t S_opt)
 {
-    l.S = S_opt > 0 ? S_opt : kDefaultS;
+    l.S = S_opt > 0 ? S_opt : auto_bunch_tiles(l.ntiles);
     l.nbunches = (l.ntiles + l.S - 1) / l.S;
 }
 

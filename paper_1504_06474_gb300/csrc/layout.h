@@ -14,6 +14,16 @@ namespace ssspmv {
 // handed out dynamically, balance tiles that differ in cost (many empty rows)
 constexpr int32_t kDefaultS = 4;
 
+// the automatic S of a single product: kDefaultS, but fewer for small
+// matrices so that their bunches still spread over a wave of resident warps
+// (about 4096 on a large GPU); the same on every device, so the workspace
+// size does not depend on it
+inline int32_t auto_bunch_tiles(int64_t ntiles)
+{
+    const int64_t s = (ntiles + 4095) / 4096;
+    return (int32_t)(s < 1 ? 1 : (s > kDefaultS ? kDefaultS : s));
+}
+
 struct Layout {
     int32_t W = 0, L = 0, S = 0;
     int64_t ntiles = 0, nbunches = 0, nbunch_cap = 0;
