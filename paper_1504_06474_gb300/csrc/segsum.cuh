@@ -246,7 +246,9 @@ constexpr uint32_t kInfoSegMask = 0x3fffffffu;
 
 // ---------------------------------------------------------------------------
 // descriptor scan of rows [rb0, stop] for tiles over many (mostly empty) rows,
-// four chunks of 32 rows per round trip.  Kept out of line: the call is rare
+// four chunks of 32 rows per round trip.  A run of empty rows shares one row
+// pointer: only its last row (the non-empty row, or `stop`) sets the bit, so
+// the atomics do not pile up on one word.  Kept out of line: the call is rare
 // and the loop then keeps its loads in flight with registers of its own
 // instead of competing with the tile's gathered x.  Returns bit 0: an empty
 // row in [rb0, stop); bit 1: row `stop` starts inside the tile.  With exact
@@ -257,7 +259,7 @@ __device__ __noinline__ uint32_t scan_rows_long(const int32_t *__restrict__ row_
                                                 uint32_t *desc, int32_t *rowmap, Y *y,
                                                 double alpha, double beta, int32_t axpby)
 {
-    constexpr int CH = 4;
+    constexpr int CH = 4;  // more would spill the FP64 kernel's registers
     const int lane = threadIdx.x & 31;
     const int32_t e = b + len;
     uint32_t flags = 0;
@@ -279,7 +281,8 @@ __device__ __noinline__ uint32_t scan_rows_long(const int32_t *__restrict__ row_
             if (lane == 31) nx = (u < CH - 1) ? nlead : tail;
             if (r <= stop) {
                 const int32_t k = pr - b;
-                if (k >= 0 && k < len) atomicOr(&desc[k >> 5], 1u << (k & 31));
+                if (k >= 0 && k < len && (r == stop || nx != pr))
+                    atomicOr(&desc[k >> 5], 1u << (k & 31));
                 if (r < stop) {
                     if (nx == pr) {
                         flags |= 1u;
@@ -302,6 +305,9 @@ __device__ __noinline__ uint32_t scan_rows_long(const int32_t *__restrict__ row_
 // split evenly this way, so the copy stream of a warp runs through memory in
 // order), then takes the remaining bunches one at a time from a ticket
 // counter, which evens out bunches that cost more (tiles over many rows).
+// Tickets run from the last bunch backwards: the sparse end of a matrix
+// (tiles over many, mostly empty rows) is started first, not left to the
+// tail of the launch.
 
 template <class P, int W, int B, int MINB, bool EXACT, bool BATCHED = false>
 __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a)
@@ -408,7 +414,8 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
         }
         request_ticket();
         tk_pending = false;
-        nxt = dyn_base + (int32_t)__shfl_sync(FULL, tk, 0);
+        const int32_t k = (int32_t)__shfl_sync(FULL, tk, 0);
+        nxt = k < nb - dyn_base ? nb - 1 - k : nb;
         if (BATCHED && nxt < nb) ni = mat_of(nxt);
     };
 
@@ -559,7 +566,9 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
             auto scan_row = [&](int32_t r, int32_t pr, int32_t nx) {
                 if (r > stop) return;
                 const int32_t k = pr - b;
-                if (k >= 0 && k < len) atomicOr(&desc[k >> 5], 1u << (k & 31));
+                // one bit per distinct pointer: set by the last row of a run
+                if (k >= 0 && k < len && (r == stop || nx != pr))
+                    atomicOr(&desc[k >> 5], 1u << (k & 31));
                 if (r < stop) {
                     if (nx == pr) {
                         dirty = true;
@@ -785,7 +794,7 @@ constexpr int kCalibWarps = 8;
 // the s-th non-empty row inside (start, stop), and the empty rows there become
 // 0.  The K partials are first copied to the warp's shared buffer `part`
 // (K <= L), so the rows can then be written in any order: the warp walks them
-// forwards, four chunks of 32 rows per round trip of row pointers.
+// forwards, eight chunks of 32 rows per round trip of row pointers.
 // t is the tile's index in its matrix and tile_offset that matrix's offsets.
 template <class P>
 __device__ __forceinline__ void repair_dirty_tile(const int32_t *__restrict__ row_ptr,
@@ -810,18 +819,19 @@ __device__ __forceinline__ void repair_dirty_tile(const int32_t *__restrict__ ro
     for (int32_t q = 1 + lane; q <= K; q += 32) part[q] = y[start + q];
     __syncwarp();
     auto rp = [&](int32_t r) { return __ldg(row_ptr + (r < m ? r : m)); };
+    constexpr int CH = 8;
     int32_t before = 0;  // non-empty rows in (start, r) so far
-    for (int32_t rb = start + 1; rb < stop; rb += 128) {
-        int32_t pr[4];
+    for (int32_t rb = start + 1; rb < stop; rb += 32 * CH) {
+        int32_t pr[CH];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) pr[u] = rp(rb + 32 * u + lane);
-        const int32_t tail = (lane == 31) ? rp(rb + 128) : 0;
+        for (int u = 0; u < CH; ++u) pr[u] = rp(rb + 32 * u + lane);
+        const int32_t tail = (lane == 31) ? rp(rb + 32 * CH) : 0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < CH; ++u) {
             const int32_t r = rb + 32 * u + lane;
-            const int32_t lead = __shfl_sync(FULL, pr[u < 3 ? u + 1 : 3], 0);
+            const int32_t lead = __shfl_sync(FULL, pr[u < CH - 1 ? u + 1 : CH - 1], 0);
             int32_t nx = __shfl_down_sync(FULL, pr[u], 1);
-            if (lane == 31) nx = (u < 3) ? lead : tail;
+            if (lane == 31) nx = (u < CH - 1) ? lead : tail;
             const bool valid = r < stop;
             const bool ne = valid && nx > pr[u];
             const unsigned mask = __ballot_sync(FULL, ne);
