@@ -248,12 +248,8 @@ def run_ours(args):
         step(plain)
     torch.cuda.synchronize(dev)
 
-    # per-step stage boundaries recorded by the library's own events on the
-    # launching stream
+    # each step timed by events on the launching stream around the whole call
     K = args.steps
-    timer = C.ssspmv_timer_create(K)
-    opts_t = C.make_opts(W=args.tile_w, S=args.tile_s, timer=timer, variant=args.variant)
-
     sampler = ClockSampler(local)
     if world > 1:
         dist.barrier()
@@ -261,22 +257,28 @@ def run_ours(args):
     sampler.start()
     time.sleep(0.25)
     t_wall = time.perf_counter()
-    for k in range(K):
-        flush_l2()
-        step(opts_t)
-    torch.cuda.synchronize(dev)
+    per_step = _event_loop(lambda: step(plain), flush_l2, K, stream)        # ms
     t_wall = time.perf_counter() - t_wall
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    times = C.ssspmv_timer_read(timer, K)
-    C.ssspmv_timer_destroy(timer)
-    assert len(times) == K
 
+    # stage breakdown: the library's own events at the kernel boundaries, in a
+    # run of its own (events between the kernels keep kernels (b) and (c)
+    # from starting early, so these steps are a little longer)
+    Ks = min(K, 200)
+    timer = C.ssspmv_timer_create(Ks)
+    opts_t = C.make_opts(W=args.tile_w, S=args.tile_s, timer=timer, variant=args.variant)
+    for k in range(Ks):
+        flush_l2()
+        step(opts_t)
+    torch.cuda.synchronize(dev)
+    times = C.ssspmv_timer_read(timer, Ks)
+    C.ssspmv_timer_destroy(timer)
+    assert len(times) == Ks
     part = [t[0] for t in times]                                             # ms
     seg = [t[1] for t in times]
     cal = [t[2] for t in times]
-    per_step = [t[3] for t in times]
     t_total = sum(per_step) / 1e3                                            # s
     if world > 1:
         tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
@@ -321,7 +323,7 @@ def run_ours(args):
         raise RuntimeError("device status bits %#x" % status)
 
     hbm, peak_kind = peaks()
-    seg_ms = sum(seg) / K
+    seg_ms = sum(seg) / Ks
     achieved = nbytes / (seg_ms / 1e3) / 1e9
     traffic = ncu_traffic("segsum_kernel", args.workload)
     line = None
@@ -341,14 +343,17 @@ def run_ours(args):
                        "W": shape["W"], "L": shape["L"], "S": shape["S"],
                        "variant": ["default", "speculative", "exact", "rows"][args.variant],
                        "bunches": shape["nbunches"], "bytes_per_step": nbytes,
+                       "ms_per_step_median": round(statistics.median(per_step), 5),
                        "paper_bytes_per_step": paper_bytes(A.m, A.nnz),
                        "hbm_frac": round(value / world / hbm, 4),
                        "gflops": round(2.0 * A.nnz * K * world / t_total / 1e9, 3),
                        "l2": ("not flushed (hot: inputs stay in L2 between steps)" if args.hot else
                               "flushed between steps (512 MB write then read, outside the timed events)"),
-                       "stage_ms": {"partition": round(sum(part) / K, 5),
+                       "stage_ms": {"partition": round(sum(part) / Ks, 5),
                                     "segsum": round(seg_ms, 5),
-                                    "calibrate": round(sum(cal) / K, 5)},
+                                    "calibrate": round(sum(cal) / Ks, 5),
+                                    "steps": Ks,
+                                    "whole": round(sum(t[3] for t in times) / Ks, 5)},
                        "wall_s_timed_loop": round(t_wall, 3)},
             "roofline": {"bound": "hbm", "kernel": "segsum_kernel",
                          "achieved": round(achieved, 2), "peak": hbm, "unit": "GB/s",
@@ -368,6 +373,22 @@ def run_ours(args):
 
 # ---------------------------------------------------------------------------
 # reduced precision (FP32 val/x/y, or BF16 val with FP32 x/y) on one matrix
+
+def _event_loop(step, flush_l2, K, stream):
+    """K steps, each after an L2 flush outside the timed region, timed by
+    events on the launching stream around the step (no host wait between
+    steps); returns the per-step device times (ms)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    for e0, e1 in ev:
+        flush_l2()
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return [e0.elapsed_time(e1) for e0, e1 in ev]
+
 
 def _timed_loop(step, flush_l2, K, stream):
     """K steps, each after an L2 flush outside the timed region; returns the
@@ -450,22 +471,25 @@ def run_precision(args):
     for _ in range(args.warmup):
         step()
     K = args.steps
-    timer = C.ssspmv_timer_create(K)
+    sampler = ClockSampler(local)
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    time.sleep(0.25)
+    per_step = _event_loop(step, flush_l2, K, stream)
+    clocks = sampler.stop()
+    whole = sum(per_step) / K
+    # stage breakdown from the library's events, in a run of its own
+    Ks = min(K, 200)
+    timer = C.ssspmv_timer_create(Ks)
     opts_t = C.make_opts(W=args.tile_w, S=args.tile_s, variant=args.variant, timer=timer)
 
     def step_t():
         C.check(fn(A.m, A.n, A.nnz, rp, col, val, xd, y, opts=opts_t, workspace=ws,
                    stream=stream), "reduced-precision call")
-    sampler = ClockSampler(local)
-    torch.cuda.synchronize(dev)
-    sampler.start()
-    time.sleep(0.25)
-    _timed_loop(step_t, flush_l2, K, stream)
-    clocks = sampler.stop()
-    t = C.ssspmv_timer_read(timer, K)
+    _timed_loop(step_t, flush_l2, Ks, stream)
+    t = C.ssspmv_timer_read(timer, Ks)
     C.ssspmv_timer_destroy(timer)
-    whole = sum(v[3] for v in t) / K
-    seg = sum(v[1] for v in t) / K
+    seg = sum(v[1] for v in t) / Ks
     nbytes = algorithmic_bytes(A.m, A.n, A.nnz, val_bytes=vb, y_bytes=4, x_bytes=4)
     value = nbytes / (whole / 1e3) / 1e9
     # the plain FP64 call on the same matrix, same GPU, same timing
@@ -524,9 +548,11 @@ def run_precision(args):
                    "n": A.n, "nnz": A.nnz, "W": shape["W"], "S": shape["S"],
                    "bytes_per_step": nbytes, "hbm_frac": round(value / hbm, 4),
                    "accumulation": "compensated FP32 pairs (TwoProduct + TwoSum)",
-                   "stage_ms": {"partition": round(sum(v[0] for v in t) / K, 5),
+                   "stage_ms": {"partition": round(sum(v[0] for v in t) / Ks, 5),
                                 "segsum": round(seg, 5),
-                                "calibrate": round(sum(v[2] for v in t) / K, 5)},
+                                "calibrate": round(sum(v[2] for v in t) / Ks, 5),
+                                "steps": Ks, "whole": round(sum(v[3] for v in t) / Ks, 5)},
+                   "ms_per_step_median": round(statistics.median(per_step), 5),
                    "plain_f64_ms": round(ms64, 5), "speedup_vs_plain_f64": round(ms64 / whole, 3),
                    "l2": "flushed between steps (512 MB write then read, outside the timed events)"},
         "roofline": {"bound": "hbm", "kernel": "segsum_kernel",

@@ -32,6 +32,27 @@ int device_sm_count();                 // api.cu: SMs of the current device (cac
 
 constexpr int kZeroBlocks = 32;
 
+// launches a kernel that may start while the kernel before it on the stream
+// finishes (programmatic dependent launch): the kernel calls grid_dep_wait()
+// before it reads anything that kernel wrote.  Kernels (b) and (c) are
+// launched this way, which hides most of a launch's latency.
+template <class... Params, class Arg>
+cudaError_t launch_dependent(void (*kernel)(Params...), unsigned grid, unsigned block,
+                             size_t smem, cudaStream_t stream, const Arg &arg)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, arg);
+}
+
 // resident warps per SM of kernel (b) for this tile shape when launched with
 // blocks of bw warps (cached per device and block size)
 template <class P, int W>
@@ -191,7 +212,8 @@ int run_shape(const Call &c)
         if (nw > l.nbunches) nw = l.nbunches;
         if (nw < 1) nw = 1;
         const unsigned grid = (unsigned)((nw + bw - 1) / bw);
-        kb<<<grid, bw * 32, bw * SM::BYTES, c.stream>>>(a);
+        e = launch_dependent(kb, grid, bw * 32, bw * SM::BYTES, c.stream, a);
+        if (e != cudaSuccess) return record_cuda_error(e);
     }
     if (c.dbg_yspec && c.m > 0) {
         e = cudaMemcpyAsync(c.dbg_yspec, c.y, sizeof(typename P::y_t) * (size_t)c.m,
@@ -229,7 +251,8 @@ int run_shape(const Call &c)
         const unsigned grid = (unsigned)(a.nblk_tiles + a.nblk_sync + a.nblk_zero);
         const size_t smem = calib_smem_bytes<P>(l.L);
         if ((e = calib_smem_attr<P, false>(smem)) != cudaSuccess) return record_cuda_error(e);
-        calibrate_kernel<P><<<grid, kCalibWarps * 32, smem, c.stream>>>(a);
+        e = launch_dependent(calibrate_kernel<P, false>, grid, kCalibWarps * 32, smem, c.stream, a);
+        if (e != cudaSuccess) return record_cuda_error(e);
     }
     if (c.ev && (e = cudaEventRecord(c.ev[3], c.stream)) != cudaSuccess)
         return record_cuda_error(e);

@@ -18,6 +18,7 @@ __global__ void __launch_bounds__(kPartitionThreads)
     partition_kernel(const int32_t *__restrict__ row_ptr, int32_t m, int32_t nnz, int32_t L,
                      int64_t ntiles, int32_t *__restrict__ tile_offset, uint32_t *err)
 {
+    grid_dep_trigger();  // kernel (b) may launch its blocks as these finish
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) {
         err[0] = 0u;  // device error word
@@ -47,6 +48,7 @@ __global__ void __launch_bounds__(kPartitionThreads)
                              int64_t ntiles, int32_t *__restrict__ tile_offset, uint32_t *err)
 {
     constexpr int64_t L = 32 * W;  // a compile-time divisor
+    grid_dep_trigger();  // kernel (b) may launch its blocks as these finish
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i0 == 0) {

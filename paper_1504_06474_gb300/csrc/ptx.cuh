@@ -109,6 +109,15 @@ __device__ __forceinline__ float ldg_keep(const float *p, uint64_t pol)
     return v;
 }
 
+// programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialization attribute may start while the kernel before it on the
+// stream is still running.  grid_dep_wait() returns once that kernel has
+// finished and its writes are visible (at once for a normal launch);
+// grid_dep_trigger() lets the next such kernel start launching its blocks.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+__device__ __forceinline__ void grid_dep_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+
 __device__ __forceinline__ int warp_inclusive_scan(int v, int lane)
 {
 #pragma unroll

@@ -469,7 +469,17 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
         fence_mbar_init();
     }
     __syncwarp();
-    for (int s = 0; s < STAGES; ++s) issue_next();
+    if constexpr (!BATCHED) {
+        // the warp's first tile is input only (no ticket, no tile offset):
+        // its copy is under way while kernel (a) finishes; nothing kernel (a)
+        // writes is read before grid_dep_wait()
+        issue_next();
+        grid_dep_wait();
+        grid_dep_trigger();
+        for (int s = 1; s < STAGES; ++s) issue_next();
+    } else {
+        for (int s = 0; s < STAGES; ++s) issue_next();
+    }
 
     // boundary rows and the first row-pointer chunk of the next tile, loaded
     // one tile ahead (rows past m read row_ptr[m])
@@ -870,6 +880,7 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
 {
     using Y = typename P::y_t;
     using A = typename P::acc_t;
+    grid_dep_wait();  // everything below reads kernel (b)'s results
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     extern __shared__ __align__(16) unsigned char calib_smem[];
