@@ -252,12 +252,12 @@ constexpr uint32_t kInfoSegMask = 0x3fffffffu;
 // and the loop then keeps its loads in flight with registers of its own
 // instead of competing with the tile's gathered x.  Returns bit 0: an empty
 // row in [rb0, stop); bit 1: row `stop` starts inside the tile.  With exact
-// stores it also writes the position-to-row map and zeroes the empty rows.
-template <bool EXACT, class Y>
+// stores (xs) it also writes the position-to-row map and zeroes the empty rows.
+template <class Y>
 __device__ __noinline__ uint32_t scan_rows_long(const int32_t *__restrict__ row_ptr, int32_t m,
                                                 int32_t rb0, int32_t stop, int32_t b, int32_t len,
                                                 uint32_t *desc, int32_t *rowmap, Y *y,
-                                                double alpha, double beta, int32_t axpby)
+                                                double alpha, double beta, int32_t axpby, bool xs)
 {
     constexpr int CH = 4;  // more would spill the FP64 kernel's registers
     const int lane = threadIdx.x & 31;
@@ -286,8 +286,8 @@ __device__ __noinline__ uint32_t scan_rows_long(const int32_t *__restrict__ row_
                 if (r < stop) {
                     if (nx == pr) {
                         flags |= 1u;
-                        if (EXACT) y[r] = scaled_store_value(y, r, Y(0), alpha, beta, axpby);
-                    } else if (EXACT && k > 0) {
+                        if (xs) y[r] = scaled_store_value(y, r, Y(0), alpha, beta, axpby);
+                    } else if (xs && k > 0) {
                         rowmap[k] = r;
                     }
                 }
@@ -570,6 +570,7 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
             // row starting there goes into the stage's column region (free
             // once the gathers above are issued) and empty rows are zeroed.
             int32_t *rowmap = reinterpret_cast<int32_t *>(st + SM::VAL_REGION);
+            constexpr bool xs = EXACT;
             if (lane <= W) desc[lane] = 0u;
             __syncwarp();
             bool dirty = false, cont = false, raw0 = false;
@@ -583,8 +584,8 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
                     if (nx == pr) {
                         dirty = true;
                         // r > start: row `start` is never empty
-                        if (EXACT) y[r] = scaled_store_value(y, r, Y(0), a.alpha, a.beta, a.axpby);
-                    } else if (EXACT && k > 0) {
+                        if (xs) y[r] = scaled_store_value(y, r, Y(0), a.alpha, a.beta, a.axpby);
+                    } else if (xs && k > 0) {
                         rowmap[k] = (int32_t)r;
                     }
                 }
@@ -603,9 +604,9 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
                 if (lane == 31 && start + 63 < stop) nx = rp_at(start + 64);
                 scan_row(start + 32 + lane, pr_chunk2, nx);
                 if (start + 64 <= stop) {  // long row ranges
-                    const uint32_t f = scan_rows_long<EXACT, Y>(row_ptr, mrows, start + 64, stop,
-                                                                b, len, desc, rowmap, y, a.alpha,
-                                                                a.beta, a.axpby);
+                    const uint32_t f = scan_rows_long<Y>(row_ptr, mrows, start + 64, stop, b, len,
+                                                         desc, rowmap, y, a.alpha, a.beta, a.axpby,
+                                                         xs);
                     dirty |= (f & 1u) != 0;
                     cont |= (f & 2u) != 0;
                 }
@@ -614,7 +615,7 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
             cont = __any_sync(FULL, cont);
             raw0 = __any_sync(FULL, raw0);
             __syncwarp();
-            const bool resolve = EXACT && dirty;
+            const bool resolve = xs && dirty;
             const int bit0 = lane * W;
             const uint64_t win =
                 ((uint64_t)desc[(bit0 >> 5) + 1] << 32) | (uint64_t)desc[bit0 >> 5];
@@ -632,13 +633,13 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
             // segment sidx goes to the synchronizer slot (the bunch's first
             // segment), to its speculative row start + sidx (Alg. 1), or --
             // exact stores on a dirty tile -- to the row that starts at its
-            // head position hpos
+            // head position hpos (read only then)
             auto emit = [&](int sidx, A v, int hpos) {
                 if (sidx == 0 && start == rF) {
                     *slot_f = v;
                 } else {
                     int32_t row = start + sidx;
-                    if (EXACT && resolve) row = hpos <= 0 ? start : rowmap[hpos < L ? hpos : 0];
+                    if (resolve) row = hpos <= 0 ? start : rowmap[hpos < L ? hpos : 0];
                     if (row >= 0 && row < mrows) {
                         if constexpr (EXACT)
                             y[row] = scaled_store_value(y, row, P::out(v), a.alpha, a.beta, a.axpby);
@@ -651,8 +652,9 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
 
             // ---- per-lane sequential segmented sum, one FMA per entry in one
             // chain (the FP64 pipe, not the chain's latency, sets the pace)
+            // head positions, where exact stores need them, come from hb: the
+            // lane's heads are at tile positions lane*W + (set bits of hb)
             A acc = P::zero(), pre = P::zero();
-            int pos = -1;  // tile position of the lane's last head (EXACT)
             if (!__any_sync(FULL, c > 1)) {
                 // at most one head per lane: it splits the run into the part
                 // before it (pre) and the segment it opens (acc); selects only
@@ -663,7 +665,6 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
                     acc = h ? ((i == 0 && lane == 0) ? cin : P::zero()) : acc;
                     acc = P::fma(vs[lane * W + i], xv[i], acc);
                 }
-                if (EXACT && c) pos = lane * W + __ffs(hb) - 1;
             } else {
                 // general case: a head closes the open segment (the part
                 // before the lane's first head belongs to an earlier segment)
@@ -671,10 +672,12 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
 #pragma unroll
                 for (int i = 0; i < W; ++i) {
                     if ((hb >> i) & 1u) {
-                        if (cur >= idx0) emit(cur, acc, pos);
+                        // the closed segment opened at the lane's previous head
+                        if (cur >= idx0)
+                            emit(cur, acc,
+                                 resolve ? lane * W + 31 - __clz(hb & ((1u << i) - 1u)) : 0);
                         else pre = acc;
                         ++cur;
-                        if (EXACT) pos = lane * W + i;
                         acc = (i == 0 && lane == 0) ? cin : P::zero();
                     }
                     acc = P::fma(vs[lane * W + i], xv[i], acc);
@@ -707,8 +710,8 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
             }
             const A Cprev = P::shfl_up(C, 1);
             int prevpos = -1, openpos = -1;
-            if (EXACT) {  // head positions of the segments left open
-                const int lastpos = pos;
+            if (resolve) {  // head positions of the segments left open
+                const int lastpos = c ? lane * W + 31 - __clz(hb) : -1;
                 const unsigned below = hm & ((1u << lane) - 1u);
                 prevpos = __shfl_sync(FULL, lastpos, below ? 31 - __clz(below) : 0);
                 openpos = __shfl_sync(FULL, lastpos, first);
