@@ -186,6 +186,7 @@ int run_shape(const Call &c)
         a.tail_flag = tflag;
         a.err = err;
         a.ticket = err + 1;
+        a.spread = err + 2;
         a.dbg_desc = c.dbg_desc;
         a.m = c.m;
         a.nnz = c.nnz;
@@ -248,6 +249,8 @@ int run_shape(const Call &c)
         a.axpby = c.axpby;
         a.nblk_sync = (int32_t)((l.nbunches + 32 * kCalibWarps - 1) / (32 * kCalibWarps));
         a.nblk_zero = kZeroBlocks;
+        // the flag of kernel (a) is the plan's when the partition is reused
+        a.spread_reset = c.skip_partition ? nullptr : err + 2;
         const unsigned grid = (unsigned)(a.nblk_tiles + a.nblk_sync + a.nblk_zero);
         const size_t smem = calib_smem_bytes<P>(l.L);
         if ((e = calib_smem_attr<P, false>(smem)) != cudaSuccess) return record_cuda_error(e);

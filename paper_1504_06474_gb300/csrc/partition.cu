@@ -23,6 +23,7 @@ __global__ void __launch_bounds__(kPartitionThreads)
     if (t == 0) {
         err[0] = 0u;  // device error word
         err[1] = 0u;  // bunch ticket of kernel (b)
+        err[2] = 1u;  // tiles span 64 rows on average: spread the schedule
     }
     if (t > ntiles) return;
     const int64_t bl = t * (int64_t)L;
@@ -71,6 +72,12 @@ __global__ void __launch_bounds__(kPartitionThreads)
             // tiles t with lo <= t*L < hi; a row spanning many tiles is
             // written by the whole warp
             const int64_t r = r0 + u * stride;
+            // 32 consecutive empty rows (sampled: first chunk of four): flag
+            // for kernel (b)'s schedule (err[2] is cleared by kernel (c) of
+            // the call before)
+            if (u == 0 &&
+                __ballot_sync(0xffffffffu, lo[u] != hi[u] || r >= m) == 0u && (threadIdx.x & 31) == 0)
+                err[2] = 1u;
             const int64_t tlo = ((uint32_t)lo[u] + (uint32_t)(L - 1)) / (uint32_t)L;
             const int64_t thi = ((uint32_t)hi[u] + (uint32_t)(L - 1)) / (uint32_t)L;
             const bool longrow = thi - tlo > 8;

@@ -145,7 +145,8 @@ struct WarpSmem {
     static constexpr int DESC_OFF = BAR_OFF + STAGES * 8;
     static constexpr int DESC_WORDS = W + 1;  // one spare word for 64-bit windows
     static constexpr int SLOT_OFF = (DESC_OFF + DESC_WORDS * 4 + 15) & ~15;
-    static constexpr int BYTES = (SLOT_OFF + 32 + 127) & ~127;
+    // slot: the bunch-first partial, the transmitter, the warp's schedule
+    static constexpr int BYTES = (SLOT_OFF + 48 + 127) & ~127;
 };
 
 // Warps per block (B) and blocks per SM maximising resident warps per SM for
@@ -211,6 +212,9 @@ struct SegsumArgs {
     int32_t *tail_flag;
     uint32_t *err;
     uint32_t *ticket;    // bunch ticket counter, zero at launch
+    // nullable: nonzero when kernel (a) saw a run of 32 empty rows (tiles
+    // over thousands of rows may follow): a smaller static share then
+    const uint32_t *spread = nullptr;
     uint32_t *dbg_desc;  // nullable
     int32_t m;
     int32_t nnz;
@@ -341,13 +345,25 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
     const int32_t nwarps = (int32_t)gridDim.x * bw;
     const int32_t g = (int32_t)blockIdx.x * bw + warp;
     if (g >= nb) return;
-    // static share: bunches [g*Q, (g+1)*Q); bunches from nwarps*Q on are
-    // handed out by ticket
+    // static share: bunches [g*Q, g*Q + Qs) (Qs = Q, 3/4 of the bunches in
+    // all); the bunches from nwarps*Q on are handed out by ticket, the last
+    // first.  When kernel (a) flags runs of empty rows, a bunch may cost as
+    // much as a whole static share, so only the first third of each share
+    // is kept (Qs) and the rest of the shares joins the ticket pool behind
+    // the end of the matrix; the first bunch of a warp is the same either way
     int32_t Q = (int32_t)((3 * (int64_t)nb) / (4 * (int64_t)nwarps));
     if (Q < 1) Q = 1;
-    const int32_t static_end = (g + 1) * Q;
     const int32_t dyn_base = nwarps * Q;
     int32_t cur = g * Q;
+    int32_t static_end = cur + Q;  // set again once kernel (a) has finished
+    // {Q, gap}, gap being the bunches of each share given to the pool: read
+    // from the warp's shared slot once the pool's tail part is used up
+    volatile int32_t *sched = reinterpret_cast<volatile int32_t *>(base + SM::SLOT_OFF + 32);
+    if (lane == 0) {
+        sched[0] = Q;
+        sched[1] = 0;
+    }
+    __syncwarp();
 
     // the matrix of the current bunch (in a batch: reloaded per bunch);
     // tbase is the global index of its first tile, shift its index in the
@@ -415,7 +431,26 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
         request_ticket();
         tk_pending = false;
         const int32_t k = (int32_t)__shfl_sync(FULL, tk, 0);
-        nxt = k < nb - dyn_base ? nb - 1 - k : nb;
+        // the static share is over for good: a bunch of the pool (a share's
+        // gap may lie below this share) is never continued as if static
+        static_end = 0;
+        if (k < nb - dyn_base) {
+            nxt = nb - 1 - k;
+        } else {
+            // the j-th bunch of the shares' gaps (share g' gives up its last
+            // gap bunches): j / gap through a float reciprocal and one
+            // correction (exact: j and gap are below 2^24), which costs
+            // fewer registers than an integer division
+            const int32_t j = k - (nb - dyn_base), gap = sched[1];
+            nxt = nb;
+            if (gap > 0 && j < (int32_t)gridDim.x * (int32_t)(blockDim.x >> 5) * gap) {
+                int32_t w = __float2int_rz((float)j * __frcp_rn((float)gap));
+                if ((w + 1) * gap <= j) ++w;
+                if (w * gap > j) --w;
+                const int32_t q = sched[0];
+                nxt = w * q + (q - gap) + (j - w * gap);
+            }
+        }
         if (BATCHED && nxt < nb) ni = mat_of(nxt);
     };
 
@@ -476,6 +511,13 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
         issue_next();
         grid_dep_wait();
         grid_dep_trigger();
+        // kernel (a)'s schedule flag (shares of fewer than 6 bunches stay
+        // whole: the flag is not read then)
+        if (Q >= 6 && a.spread != nullptr && *(volatile const uint32_t *)a.spread != 0u) {
+            static_end = cur + Q / 3;
+            if (lane == 0) sched[1] = Q - Q / 3;
+            __syncwarp();
+        }
         for (int s = 1; s < STAGES; ++s) issue_next();
     } else {
         for (int s = 0; s < STAGES; ++s) issue_next();
@@ -620,7 +662,9 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
             const uint64_t win =
                 ((uint64_t)desc[(bit0 >> 5) + 1] << 32) | (uint64_t)desc[bit0 >> 5];
             uint32_t hb = (uint32_t)(win >> (bit0 & 31)) & ((1u << W) - 1u);
-            if (a.dbg_desc != nullptr && lane < W) a.dbg_desc[t * W + lane] = desc[lane];
+            // debug export, added to a zeroed buffer: a tile processed twice
+            // would show doubled words
+            if (a.dbg_desc != nullptr && lane < W) atomicAdd(a.dbg_desc + t * W + lane, desc[lane]);
             if (lane == 0) hb |= 1u;  // each tile opens with a segment (Sec. 3.2)
 
             // ---- compact indices: exclusive scan of head counts (y_index)
@@ -791,6 +835,7 @@ struct CalibArgs {
     int32_t nblk_sync;
     int32_t nblk_zero;
     int32_t span;  // tiles per warp window of the tile role (1..32)
+    uint32_t *spread_reset = nullptr;  // kernel (b)'s schedule flag, cleared here
     double alpha = 1.0, beta = 0.0;  // y = alpha A x + beta y (see SegsumArgs)
     int32_t axpby = 0;
     // batches only (see SegsumArgs)
@@ -884,6 +929,7 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
     using Y = typename P::y_t;
     using A = typename P::acc_t;
     grid_dep_wait();  // everything below reads kernel (b)'s results
+    if (a.spread_reset != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *a.spread_reset = 0u;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     extern __shared__ __align__(16) unsigned char calib_smem[];

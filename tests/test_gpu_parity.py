@@ -111,6 +111,22 @@ def test_block_warps(dev, bw):
         check_case(dev, A.row_ptr, A.col, A.val, x, A.n, W=W, block_warps=bw)
 
 
+def test_spread_schedule(dev):
+    """R-MAT at scale 20 with one tile per bunch: kernel (a) sees runs of 32
+    empty rows and kernel (b) keeps only a third of each static share, the
+    rest going to the ticket pool.  Every tile must be processed exactly once
+    (the descriptor export is summed, so a second visit would show) and y and
+    the index artefacts must match."""
+    A, x = synth.workload("rmat20")
+    lens = np.diff(np.asarray(A.row_ptr, np.int64))
+    # precondition: all-empty aligned 32-row chunks among the rows the
+    # partition kernel samples (the first of its four row chunks per thread)
+    first = (min(A.m, 262144) // 32) * 32
+    assert (lens[:first].reshape(-1, 32).sum(1) == 0).any()
+    for W in (15, 21):
+        check_case(dev, A.row_ptr, A.col, A.val, x, A.n, W=W, S=1)
+
+
 @pytest.mark.parametrize("seed,mean,p_empty,p_long,long_len", [
     (1, 8, 0.5, 0.0, 0),        # half the rows empty: nearly every tile dirty
     (2, 3, 0.2, 0.0, 0),        # short rows: many segments per lane
