@@ -853,19 +853,16 @@ constexpr int kCalibWarps = 8;
 // 0.  The K partials are first copied to the warp's shared buffer `part`
 // (K <= L), so the rows can then be written in any order: the warp walks them
 // forwards, eight chunks of 32 rows per round trip of row pointers.
-// t is the tile's index in its matrix and tile_offset that matrix's offsets.
+// t is the tile's index in its matrix, [start, stop] its rows.
 template <class P>
 __device__ __forceinline__ void repair_dirty_tile(const int32_t *__restrict__ row_ptr,
-                                                  typename P::y_t *__restrict__ y,
-                                                  const int32_t *__restrict__ tile_offset,
-                                                  int32_t m, int32_t nnz, int32_t L, int64_t t,
-                                                  uint32_t info, uint32_t *err, int lane,
-                                                  typename P::y_t *part)
+                                                  typename P::y_t *__restrict__ y, int32_t m,
+                                                  int32_t nnz, int32_t L, int64_t t, int32_t start,
+                                                  int32_t stop, uint32_t info, uint32_t *err,
+                                                  int lane, typename P::y_t *part)
 {
     using Y = typename P::y_t;
     const int32_t nseg = (int32_t)(info & kInfoSegMask);
-    const int32_t start = __ldg(tile_offset + t);
-    const int32_t stop = __ldg(tile_offset + t + 1);
     const int64_t e = (t + 1) * (int64_t)L < nnz ? (t + 1) * (int64_t)L : nnz;
     const bool cont = stop < m && (int64_t)__ldg(row_ptr + stop) < e;
     // non-empty rows strictly inside (start, stop): each holds one segment
@@ -909,6 +906,85 @@ __device__ __forceinline__ void repair_dirty_tile(const int32_t *__restrict__ ro
     __syncwarp();  // the buffer is reused for the warp's next tile
 }
 
+// dirty tiles over more rows than this are re-arranged by a whole block
+constexpr int32_t kLongRepairRows = 1024;
+constexpr int kLongListCap = 64;  // such tiles a block defers (more: by a warp)
+
+// the same re-arrangement by all kCalibWarps warps of a block, for a tile
+// over many rows: each warp takes a contiguous share of (start, stop), counts
+// its non-empty rows (first pass), and after a block barrier moves the
+// partials from its count prefix on (second pass).  Every thread of the block
+// calls it with the same arguments; part holds L+1 values, cnt kCalibWarps.
+template <class P>
+__device__ void repair_long_tile(const int32_t *__restrict__ row_ptr,
+                                 typename P::y_t *__restrict__ y, int32_t m, int32_t nnz,
+                                 int32_t L, int64_t t, int32_t start, int32_t stop, uint32_t info,
+                                 uint32_t *err, typename P::y_t *part, int32_t *cnt)
+{
+    using Y = typename P::y_t;
+    constexpr int CH = 8;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t nseg = (int32_t)(info & kInfoSegMask);
+    const int64_t e = (t + 1) * (int64_t)L < nnz ? (t + 1) * (int64_t)L : nnz;
+    const bool cont = stop < m && (int64_t)__ldg(row_ptr + stop) < e;
+    const int32_t K = nseg - 1 - (cont ? 1 : 0);
+    if (K < 0 || K > L) {  // the same for every thread of the block
+        if (threadIdx.x == 0) atomicOr(err, SSSPMV_DEV_CALIB);
+        return;
+    }
+    for (int32_t q = 1 + (int32_t)threadIdx.x; q <= K; q += (int32_t)blockDim.x)
+        part[q] = y[start + q];
+    auto rp = [&](int32_t r) { return __ldg(row_ptr + (r < m ? r : m)); };
+    // this warp's rows [r0, r1) of (start, stop), shares a multiple of 32
+    const int32_t n = stop - start - 1;
+    const int32_t per = ((n + kCalibWarps - 1) / kCalibWarps + 31) & ~31;
+    const int32_t r0 = start + 1 + warp * per;
+    const int32_t r1 = r0 + per < stop ? r0 + per : stop;
+    // walks [r0, r1): f(r, valid, non-empty) per row, chunk by chunk
+    auto walk = [&](auto &&f) {
+        for (int32_t rb = r0; rb < r1; rb += 32 * CH) {
+            int32_t pr[CH];
+#pragma unroll
+            for (int u = 0; u < CH; ++u) pr[u] = rp(rb + 32 * u + lane);
+            const int32_t tail = (lane == 31) ? rp(rb + 32 * CH) : 0;
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                const int32_t r = rb + 32 * u + lane;
+                const int32_t lead = __shfl_sync(FULL, pr[u < CH - 1 ? u + 1 : CH - 1], 0);
+                int32_t nx = __shfl_down_sync(FULL, pr[u], 1);
+                if (lane == 31) nx = (u < CH - 1) ? lead : tail;
+                const bool valid = r < r1;
+                f(r, valid, valid && nx > pr[u]);
+            }
+        }
+    };
+    int32_t mine = 0;
+    walk([&](int32_t, bool, bool ne) { mine += __popc(__ballot_sync(FULL, ne)); });
+    if (lane == 0) cnt[warp] = mine;
+    __syncthreads();  // counts and partials in place
+    int32_t before = 0, total = 0;
+    for (int w = 0; w < kCalibWarps; ++w) {
+        const int32_t c = cnt[w];
+        if (w < warp) before += c;
+        total += c;
+    }
+    if (threadIdx.x == 0 && total != K) atomicOr(err, SSSPMV_DEV_CALIB);
+    walk([&](int32_t r, bool valid, bool ne) {
+        const unsigned mask = __ballot_sync(FULL, ne);
+        const int32_t q = before + 1 + __popc(mask & ((1u << lane) - 1u));
+        if (valid) {
+            Y v = Y(0);
+            if (ne) {
+                if (q <= K) v = part[q];
+                else atomicOr(err, SSSPMV_DEV_CALIB);
+            }
+            y[r] = v;
+        }
+        before += __popc(mask);
+    });
+    __syncthreads();  // part and cnt are reused by the block's next tile
+}
+
 // the batch matrix holding global tile t: the last one whose first tile is
 // at or before t (matrices without tiles share the next one's base)
 __device__ __forceinline__ int32_t batch_matrix_of_tile(const BatchMat *mats, int32_t count,
@@ -945,30 +1021,72 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
         // (warp w takes tiles w, w + nw, w + 2 nw, ...: dirty tiles cluster,
         // so striding spreads them over the warps; `span` of them are read in
         // one round of loads, then the dirty ones are repaired in turn)
+        // Consecutive tiles go to consecutive blocks (tile t to the warp with
+        // block-major index t mod nw), so tiles over many rows, which
+        // cluster, spread over the blocks: each warp defers those to its
+        // block, which re-arranges them with all its warps at the end.
+        __shared__ int64_t s_long[kLongListCap];
+        __shared__ uint32_t s_linfo[kLongListCap];
+        __shared__ int32_t s_nlong, s_cnt[kCalibWarps];
+        if (threadIdx.x == 0) s_nlong = 0;
+        __syncthreads();
         const int64_t nw = (int64_t)a.nblk_tiles * kCalibWarps;
         const int64_t span = a.span;
-        for (int64_t t0 = (int64_t)blk * kCalibWarps + warp; t0 < ntiles; t0 += nw * span) {
-            const int64_t tl = t0 + (int64_t)lane * nw;
-            const uint32_t il = (lane < span && tl < ntiles) ? __ldg(a.tile_info + tl) : 0u;
-            unsigned todo = __ballot_sync(FULL, (il & kInfoDirty) && !(il & kInfoResolved));
-            while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int64_t t = t0 + (int64_t)src * nw;
-            const uint32_t info = __shfl_sync(FULL, il, src);
+        // the matrix data of global tile t (in a batch: of its matrix)
+        struct Tile {
+            const int32_t *row_ptr;
+            Y *y;
+            int32_t m, nnz, start, stop;
+            int64_t t;  // in its matrix
+        };
+        auto tile_of = [&](int64_t t) -> Tile {
             if constexpr (BATCHED) {
                 const int32_t mi = batch_matrix_of_tile(a.mats, a.count, t);
                 const BatchMat *mm = a.mats + mi;
                 const int32_t tb = __ldg(&mm->tile_base);
-                repair_dirty_tile<P>(ldg_ptr(&mm->row_ptr),
-                                     static_cast<Y *>(ldg_ptr(const_cast<void *const *>(&mm->y))),
-                                     a.tile_offset + tb + mi, __ldg(&mm->m), __ldg(&mm->nnz), a.L,
-                                     t - tb, info, a.err, lane, part);
+                const int32_t *to = a.tile_offset + tb + mi;  // the matrix's offsets
+                return Tile{ldg_ptr(&mm->row_ptr),
+                            static_cast<Y *>(ldg_ptr(const_cast<void *const *>(&mm->y))),
+                            __ldg(&mm->m), __ldg(&mm->nnz), __ldg(to + (t - tb)),
+                            __ldg(to + (t - tb) + 1), t - tb};
             } else {
-                repair_dirty_tile<P>(a.row_ptr, y, a.tile_offset, a.m, a.nnz, a.L, t, info, a.err,
-                                     lane, part);
+                return Tile{a.row_ptr, y, a.m, a.nnz, __ldg(a.tile_offset + t),
+                            __ldg(a.tile_offset + t + 1), t};
             }
+        };
+        for (int64_t t0 = (int64_t)warp * a.nblk_tiles + blk; t0 < ntiles; t0 += nw * span) {
+            const int64_t tl = t0 + (int64_t)lane * nw;
+            const uint32_t il = (lane < span && tl < ntiles) ? __ldg(a.tile_info + tl) : 0u;
+            unsigned todo = __ballot_sync(FULL, (il & kInfoDirty) && !(il & kInfoResolved));
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int64_t t = t0 + (int64_t)src * nw;
+                const uint32_t info = __shfl_sync(FULL, il, src);
+                const Tile T = tile_of(t);
+                if (T.stop - T.start > kLongRepairRows) {
+                    int slot = 0;
+                    if (lane == 0) slot = atomicAdd(&s_nlong, 1);
+                    slot = __shfl_sync(FULL, slot, 0);
+                    if (slot < kLongListCap) {
+                        if (lane == 0) {
+                            s_long[slot] = t;
+                            s_linfo[slot] = info;
+                        }
+                        continue;
+                    }
+                }
+                repair_dirty_tile<P>(T.row_ptr, T.y, T.m, T.nnz, a.L, T.t, T.start, T.stop, info,
+                                     a.err, lane, part);
             }
+        }
+        __syncthreads();
+        const int nlong = s_nlong < kLongListCap ? s_nlong : kLongListCap;
+        Y *bpart = reinterpret_cast<Y *>(calib_smem);  // every warp's buffer is free now
+        for (int i = 0; i < nlong; ++i) {
+            const Tile T = tile_of(s_long[i]);
+            repair_long_tile<P>(T.row_ptr, T.y, T.m, T.nnz, a.L, T.t, T.start, T.stop, s_linfo[i],
+                                a.err, bpart, s_cnt);
         }
         return;
     }

@@ -154,6 +154,8 @@ def test_random_structures(dev, seed, mean, p_empty, p_long, long_len):
     [27] * 1000 + [0] + [27] * 1000,            # lanes aligned with rows, one empty
     [961, 0, 0, 961, 1],                        # rows exactly one tile long (W=31)
     [0] * 5 + [405] * 3 + [0] * 2 + [405],      # rows aligned with 15-wide tiles
+    [3] * 100 + [0] * 5000 + [3] * 100,          # a dirty tile over 5,000 rows (block repair)
+    ([2] * 240 + [0] * 1500) * 6 + [7] * 50,     # consecutive such tiles (one per block)
     [3] + [0] * 500 + [4] + [0] * 100 + [2] * 3 + [0] * 70,   # tiles over hundreds of rows
     ([0] * 40 + [1]) * 60 + [0] * 3000,         # sparse rows, long empty tail
     [500] + [0] * 2000 + [1] * 40 + [0] * 90 + [700],       # long rows around empty runs
