@@ -95,7 +95,8 @@ extern "C" {
  * only what you need; a NULL opts pointer means all defaults. */
 typedef struct ssspmv_opts {
     int32_t W;         /* entries per lane (odd, see ssspmv_supported_w); L = 32*W.
-                          0 = the shortest compiled tile.  With SSSPMV_VARIANT_ROWS:
+                          0 = the shortest compiled tile (BF16 values: 27 when rows
+                          hold 20 entries or more on average).  With SSSPMV_VARIANT_ROWS:
                           lanes per row (see there) */
     int32_t S;         /* tiles per thread-bunch (warp); 0 = 4, or fewer for matrices of
                           under 12,288 tiles (ceil(ntiles / 4096)).  Each warp of a
