@@ -45,6 +45,27 @@ def test_host_only_queries(lib):
     assert S.ssspmv_workspace_bytes(10, 10, 3, None) == 0
 
 
+def test_default_shape_rules(lib):
+    """The defaults chosen on the host: tiles per bunch S = ceil(ntiles/4096)
+    up to 4, and the tile width (the shortest, but 27 for BF16 values when
+    rows hold 20 entries or more on average); the workspace is sized for the
+    same S, so it never depends on the device."""
+    sh = S.ssspmv_plan_shape
+    for ntiles, want in ((1, 1), (130, 1), (4096, 1), (4097, 2), (8192, 2), (12288, 3),
+                         (12289, 4), (227_532, 4)):
+        got = sh(4096, ntiles * 480, 8, None)
+        assert (got["W"], got["ntiles"], got["S"]) == (15, ntiles, want), (ntiles, got)
+        assert got["nbunches"] == -(-ntiles // want)
+    assert sh(4096, 62_167, 8, S.make_opts(S=4))["S"] == 4  # an explicit S stands
+    # tile width: BF16 values with long rows, everything else the shortest
+    assert sh(4_096_000, 109_215_352, 2, None)["W"] == 27     # stencil, 26.7 per row
+    assert sh(4_194_304, 66_242_182, 2, None)["W"] == 15      # R-MAT, 15.8 per row
+    assert sh(1000, 19_999, 2, None)["W"] == 15 and sh(1000, 20_000, 2, None)["W"] == 27
+    for vb in (8, 4):
+        assert sh(4_096_000, 109_215_352, vb, None)["W"] == 15
+    assert sh(4_096_000, 109_215_352, 2, S.make_opts(W=21))["W"] == 21
+
+
 FAKE = 0x7f0000000000  # never dereferenced: every call below fails on the host
 
 
