@@ -99,7 +99,7 @@ typedef struct ssspmv_opts {
                           hold 20 entries or more on average).  With SSSPMV_VARIANT_ROWS:
                           lanes per row (see there) */
     int32_t S;         /* tiles per thread-bunch (warp); 0 = 4, or fewer for matrices of
-                          under 12,288 tiles (ceil(ntiles / 4096)).  Each warp of a
+                          under 98,304 tiles (ceil(ntiles / 32768)).  Each warp of a
                           persistent grid first takes an even contiguous share of
                           3/4 of the bunches, then single bunches from a counter */
     int32_t block_warps; /* warps per block of the segmented-sum kernel (one block

@@ -14,13 +14,14 @@ namespace ssspmv {
 // handed out dynamically, balance tiles that differ in cost (many empty rows)
 constexpr int32_t kDefaultS = 4;
 
-// the automatic S of a single product: kDefaultS, but fewer for small
-// matrices so that their bunches still spread over a wave of resident warps
-// (about 4096 on a large GPU); the same on every device, so the workspace
-// size does not depend on it
+// the automatic S of a single product: kDefaultS, but fewer for matrices of
+// under 98,304 tiles, so that each of the ~3,000 resident warps of a large GPU
+// still gets about ten bunches and the ticket pool can balance them (and the
+// spread schedule has shares to split); the same on every device, so the
+// workspace size does not depend on it
 inline int32_t auto_bunch_tiles(int64_t ntiles)
 {
-    const int64_t s = (ntiles + 4095) / 4096;
+    const int64_t s = (ntiles + 32767) / 32768;
     return (int32_t)(s < 1 ? 1 : (s > kDefaultS ? kDefaultS : s));
 }
 

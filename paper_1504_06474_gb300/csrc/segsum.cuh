@@ -345,12 +345,13 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
     const int32_t nwarps = (int32_t)gridDim.x * bw;
     const int32_t g = (int32_t)blockIdx.x * bw + warp;
     if (g >= nb) return;
-    // static share: bunches [g*Q, g*Q + Qs) (Qs = Q, 3/4 of the bunches in
-    // all); the bunches from nwarps*Q on are handed out by ticket, the last
-    // first.  When kernel (a) flags runs of empty rows, a bunch may cost as
-    // much as a whole static share, so only the first third of each share
-    // is kept (Qs) and the rest of the shares joins the ticket pool behind
-    // the end of the matrix; the first bunch of a warp is the same either way
+    // static share: bunches [g*Q, g*Q + Q) (3/4 of the bunches in all); the
+    // bunches from nwarps*Q on are handed out by ticket, the last first.
+    // When kernel (a) flags runs of empty rows, a bunch may cost as much as a
+    // whole static share, so only the first third of each share is kept (at
+    // least one bunch) and the rest of the shares joins the ticket pool
+    // behind the end of the matrix; the first bunch of a warp is the same
+    // either way
     int32_t Q = (int32_t)((3 * (int64_t)nb) / (4 * (int64_t)nwarps));
     if (Q < 1) Q = 1;
     const int32_t dyn_base = nwarps * Q;
@@ -511,11 +512,12 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
         issue_next();
         grid_dep_wait();
         grid_dep_trigger();
-        // kernel (a)'s schedule flag (shares of fewer than 6 bunches stay
-        // whole: the flag is not read then)
-        if (Q >= 6 && a.spread != nullptr && *(volatile const uint32_t *)a.spread != 0u) {
-            static_end = cur + Q / 3;
-            if (lane == 0) sched[1] = Q - Q / 3;
+        // kernel (a)'s schedule flag (a share of one bunch stays whole: the
+        // flag is not read then); applied before the first claim
+        if (Q >= 2 && a.spread != nullptr && *(volatile const uint32_t *)a.spread != 0u) {
+            const int32_t qs = Q >= 3 ? Q / 3 : 1;
+            static_end = cur + qs;
+            if (lane == 0) sched[1] = Q - qs;
             __syncwarp();
         }
         for (int s = 1; s < STAGES; ++s) issue_next();

@@ -46,13 +46,13 @@ def test_host_only_queries(lib):
 
 
 def test_default_shape_rules(lib):
-    """The defaults chosen on the host: tiles per bunch S = ceil(ntiles/4096)
+    """The defaults chosen on the host: tiles per bunch S = ceil(ntiles/32768)
     up to 4, and the tile width (the shortest, but 27 for BF16 values when
     rows hold 20 entries or more on average); the workspace is sized for the
     same S, so it never depends on the device."""
     sh = S.ssspmv_plan_shape
-    for ntiles, want in ((1, 1), (130, 1), (4096, 1), (4097, 2), (8192, 2), (12288, 3),
-                         (12289, 4), (227_532, 4)):
+    for ntiles, want in ((1, 1), (130, 1), (32768, 1), (32769, 2), (65536, 2), (98304, 3),
+                         (98305, 4), (227_532, 4)):
         got = sh(4096, ntiles * 480, 8, None)
         assert (got["W"], got["ntiles"], got["S"]) == (15, ntiles, want), (ntiles, got)
         assert got["nbunches"] == -(-ntiles // want)
