@@ -54,7 +54,7 @@ extern "C" {
 #define SSSPMV_EWORKSPACE   -2  /* workspace NULL or smaller than ssspmv_workspace_bytes() */
 #define SSSPMV_ECUDA        -3  /* a CUDA call failed; see ssspmv_last_cuda_error() */
 #define SSSPMV_EDEVICE      -4  /* a kernel reported an inconsistency or a timed-out wait */
-#define SSSPMV_EUNSUPPORTED -5  /* tile shape not compiled in this build */
+#define SSSPMV_EUNSUPPORTED -5  /* tile shape not compiled into the library */
 #define SSSPMV_ETOOLARGE    -6  /* problem needs more scratch than ssspmv_csr_f64_noalloc has */
 
 /* Largest m and nnz accepted (larger values return SSSPMV_EINVAL): the
@@ -360,7 +360,7 @@ int ssspmv_validate_csr(int32_t m, int32_t n, int32_t nnz, const int32_t *row_pt
 int ssspmv_device_status(void *workspace, size_t ws_bytes, void *stream, int clear,
                          uint32_t *bits);
 
-/* Odd W values compiled into this build, written to out[0..*count). */
+/* Odd W values compiled into the library, written to out[0..*count). */
 int ssspmv_supported_w(int32_t *out, int32_t cap, int32_t *count);
 
 const char *ssspmv_strerror(int code);

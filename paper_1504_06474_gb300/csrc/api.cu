@@ -390,7 +390,7 @@ const char *ssspmv_strerror(int code)
     case SSSPMV_EWORKSPACE: return "workspace missing, misaligned or too small";
     case SSSPMV_ECUDA: return "CUDA error (see ssspmv_last_cuda_error)";
     case SSSPMV_EDEVICE: return "a kernel reported an error";
-    case SSSPMV_EUNSUPPORTED: return "tile shape not compiled in this build";
+    case SSSPMV_EUNSUPPORTED: return "tile shape not compiled into the library";
     case SSSPMV_ETOOLARGE:
         return "problem exceeds the fixed scratch of ssspmv_csr_f64_noalloc "
                "(SSSPMV_NOALLOC_SCRATCH_BYTES)";
