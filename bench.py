@@ -227,8 +227,27 @@ def run_ours(args):
     Ad = api.to_device(A.row_ptr, A.col, A.val, A.n, dev)
     xd = torch.as_tensor(x, device=dev)
     y = torch.empty(A.m, dtype=torch.float64, device=dev)
-    shape = C.ssspmv_plan_shape(A.m, A.nnz, 8, C.make_opts(W=args.tile_w, S=args.tile_s, variant=args.variant))
-    ws = api.workspace_for(Ad, C.make_opts(W=args.tile_w, S=args.tile_s, variant=args.variant), device=dev)
+    selected = None
+    if args.select:
+        # the shipped network's class for this matrix, from its device features
+        from paper_1504_06474_gb300 import selector as SEL
+        params = SEL.load_default()
+        if params is None:
+            raise RuntimeError("no selector weights shipped with the package")
+        f = SEL.device_features(Ad.row_ptr, A.m, A.n, A.nnz).cpu().numpy()[None, :]
+        k = int(SEL.select(params, f, dev)[0])
+        kw = SEL.CLASSES[k][1]
+        args.tile_w, args.variant = kw.get("W", 0), kw.get("variant", 0)
+        args.block_warps = kw.get("block_warps", 0)
+        selected = {"class": SEL.CLASSES[k][0], "index": k}
+
+    def mk(timer=None, W=None, variant=None, block_warps=None):
+        return C.make_opts(W=args.tile_w if W is None else W, S=args.tile_s, timer=timer,
+                           variant=args.variant if variant is None else variant,
+                           block_warps=args.block_warps if block_warps is None else block_warps)
+    rows_variant = args.variant == C.VARIANT_ROWS
+    shape = C.ssspmv_plan_shape(A.m, A.nnz, 8, mk())
+    ws = api.workspace_for(Ad, mk(), device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     sink = torch.empty(1, dtype=torch.int64, device=dev)
 
@@ -247,7 +266,7 @@ def run_ours(args):
         if rc != 0:
             raise C.SsspmvError(rc, "ssspmv_csr_f64")
 
-    plain = C.make_opts(W=args.tile_w, S=args.tile_s, variant=args.variant)
+    plain = mk()
     for _ in range(args.warmup):
         flush_l2()
         step(plain)
@@ -273,7 +292,7 @@ def run_ours(args):
     # from starting early, so these steps are a little longer)
     Ks = min(K, 200)
     timer = C.ssspmv_timer_create(Ks)
-    opts_t = C.make_opts(W=args.tile_w, S=args.tile_s, timer=timer, variant=args.variant)
+    opts_t = mk(timer=timer)
     for k in range(Ks):
         flush_l2()
         step(opts_t)
@@ -285,6 +304,22 @@ def run_ours(args):
     seg = [t[1] for t in times]
     cal = [t[2] for t in times]
     t_total = sum(per_step) / 1e3                                            # s
+    if selected is not None:
+        # the default configuration on the same matrix, timed the same way
+        dflt = mk(W=0, variant=0, block_warps=0)
+        ws_d = api.workspace_for(Ad, dflt, device=dev)
+
+        def step_d():
+            C.check(C.ssspmv_csr_f64(A.m, A.n, A.nnz, Ad.row_ptr, Ad.col, Ad.val, xd, y,
+                                     opts=dflt, workspace=ws_d, stream=stream), "default")
+        for _ in range(args.warmup):
+            flush_l2()
+            step_d()
+        d_ms = sum(_event_loop(step_d, flush_l2, Ks, stream)) / Ks
+        selected["default_ms_per_step"] = round(d_ms, 5)
+        selected["speedup_vs_default"] = round(d_ms / (t_total / K * 1e3), 4)
+        del ws_d
+        step(plain)  # y from the selected configuration again
     if world > 1:
         tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -330,7 +365,10 @@ def run_ours(args):
     hbm, peak_kind = peaks()
     seg_ms = sum(seg) / Ks
     achieved = nbytes / (seg_ms / 1e3) / 1e9
-    traffic = ncu_traffic("segsum_kernel", args.workload)
+    # the ncu record holds for the default configuration it was captured with
+    default_cfg = (not args.select and args.tile_w in (0, 15) and args.variant == 0
+                   and args.block_warps == 0 and args.tile_s in (0, 4))
+    traffic = ncu_traffic("segsum_kernel", args.workload) if default_cfg else None
     line = None
     if rank == 0:
         cpu = None
@@ -347,6 +385,7 @@ def run_ours(args):
             "config": {"workload": args.workload, "m": A.m, "n": A.n, "nnz": A.nnz,
                        "W": shape["W"], "L": shape["L"], "S": shape["S"],
                        "variant": ["default", "speculative", "exact", "rows"][args.variant],
+                       "block_warps": args.block_warps, "selector": selected,
                        "bunches": shape["nbunches"], "bytes_per_step": nbytes,
                        "ms_per_step_median": round(statistics.median(per_step), 5),
                        "paper_bytes_per_step": paper_bytes(A.m, A.nnz),
@@ -360,13 +399,14 @@ def run_ours(args):
                                     "steps": Ks,
                                     "whole": round(sum(t[3] for t in times) / Ks, 5)},
                        "wall_s_timed_loop": round(t_wall, 3)},
-            "roofline": {"bound": "hbm", "kernel": "segsum_kernel",
+            "roofline": {"bound": "hbm",
+                         "kernel": "csr_rows_kernel" if rows_variant else "segsum_kernel",
                          "achieved": round(achieved, 2), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
                          "traffic": traffic},
             "clocks": clocks,
             "e2e": e2e,
-            "gpu_launches": 3 * K,
+            "gpu_launches": (1 if rows_variant else 3) * K,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -744,6 +784,10 @@ def main():
     ap.add_argument("--workload", default="stencil160")
     ap.add_argument("--tile-w", type=int, default=0)
     ap.add_argument("--tile-s", type=int, default=0)
+    ap.add_argument("--select", action="store_true",
+                    help="FP64: tile shape and variant chosen by the shipped selector network "
+                         "(the default configuration is timed beside it)")
+    ap.add_argument("--block-warps", type=int, default=0)
     ap.add_argument("--variant", type=int, default=0,
                     help="0 default, 1 speculative + calibration, 2 exact stores, 3 row-parallel")
     ap.add_argument("--e2e-steps", type=int, default=10)
