@@ -99,7 +99,7 @@ def test_bf16_values(dev, name, spec):
     vbf = torch.as_tensor(A.val).to(torch.bfloat16)
     x32 = x.astype(np.float32)
     v_r = vbf.to(torch.float64).numpy()
-    for W in (15, 27):
+    for W in (0, 15, 27):  # 0: the default (27 for long_rows' 30 entries per row)
         y = _run(dev, A, vbf.to(dev).view(torch.int16), torch.as_tensor(x32, device=dev), "bf16",
                  W, 0)
         _check(A, x, v_r, x32.astype(np.float64), y, "bf16 %s W=%d" % (name, W))
