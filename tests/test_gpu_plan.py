@@ -171,3 +171,49 @@ def test_library_owned_workspace(dev):
     C.ssspmv_release_workspaces()
     with pytest.raises(C.SsspmvError):
         C.ssspmv_cached_workspace(s1)
+
+
+def test_spread_flag_across_calls_and_plans(dev):
+    """Kernel (b)'s schedule flag lives in the workspace: kernel (a) sets it on
+    a matrix with runs of empty rows (R-MAT scale 20, S = 1: shares of about
+    ten bunches), kernel (c) clears it, and a plan keeps the one its creation
+    set.  One workspace serves a flagged and an unflagged matrix in turn, and
+    a plan executes several times; y is exact every time and the same bit for
+    bit whatever the schedule."""
+    C = _C()
+    R, xr = synth.workload("rmat20")
+    U, xu = synth.workload("uniform4096")
+    opts = C.make_opts(S=1)
+    nbytes = max(C.ssspmv_workspace_bytes(M.m, M.nnz, 8, opts) for M in (R, U))
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    dev_of = lambda M, x: [torch.as_tensor(a, device=dev) for a in (M.row_ptr, M.col, M.val, x)]
+    Rd, Ud = dev_of(R, xr), dev_of(U, xu)
+    refs = {id(R): oracle.spmv_dot2(R.row_ptr, R.col, R.val, xr),
+            id(U): oracle.spmv_dot2(U.row_ptr, U.col, U.val, xu)}
+    first = {}
+    for M, (rp, col, val, x) in ((R, Rd), (U, Ud), (R, Rd), (R, Rd), (U, Ud)):
+        y = torch.full((M.m,), float("nan"), dtype=torch.float64, device=dev)
+        C.check(C.ssspmv_csr_f64(M.m, M.n, M.nnz, rp, col, val, x, y, opts=opts, workspace=ws),
+                "ssspmv_csr_f64")
+        assert C.ssspmv_device_status(ws) == 0
+        yh = y.cpu().numpy()
+        yref, s = refs[id(M)]
+        assert np.all(np.abs(yh - yref) <= TOL * s)
+        if id(M) in first:
+            assert np.array_equal(yh, first[id(M)])
+        first.setdefault(id(M), yh)
+    # a plan on the flagged matrix, executed after calls on the other one
+    rp, col, val, x = Rd
+    plan = C.ssspmv_plan_create(R.m, R.n, R.nnz, rp, 8, opts)
+    try:
+        for k in range(3):
+            yu = torch.empty(U.m, dtype=torch.float64, device=dev)
+            C.check(C.ssspmv_csr_f64(U.m, U.n, U.nnz, *Ud[:3], Ud[3], yu, opts=opts,
+                                     workspace=ws), "ssspmv_csr_f64")
+            y = torch.full((R.m,), float("nan"), dtype=torch.float64, device=dev)
+            C.check(C.ssspmv_plan_execute(plan, col, val, x, y), "ssspmv_plan_execute")
+            assert np.array_equal(y.cpu().numpy(), first[id(R)])
+        ptr, nb = C.ssspmv_plan_workspace(plan)
+        assert C.ssspmv_device_status(ptr, nb) == 0
+    finally:
+        C.ssspmv_plan_destroy(plan)
