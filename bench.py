@@ -148,6 +148,24 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(v: float, device=None) -> float:
+    """The largest v over the ranks of the process group (every rank calls
+    it, and every rank gets the maximum); v itself without a group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(bytes_per_step: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job GB/s of `world` replicas that each did `steps` products of
+    `bytes_per_step` in at most `seconds` (the slowest rank's time)."""
+    return bytes_per_step * steps * world / seconds / 1e9
+
+
 def cpu_oracle_rate(A, x, budget_s: float, max_reps: int = 1000):
     """Times the oracle's OpenMP row loop over the whole matrix, repeated until
     budget_s of CPU time has been spent.  Returns (GB/s, threads, reps, s)."""
@@ -320,12 +338,9 @@ def run_ours(args):
         selected["speedup_vs_default"] = round(d_ms / (t_total / K * 1e3), 4)
         del ws_d
         step(plain)  # y from the selected configuration again
-    if world > 1:
-        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
+    t_total = max_over_ranks(t_total, dev)  # the slowest replica
     nbytes = algorithmic_bytes(A.m, A.n, A.nnz)
-    value = nbytes * K * world / t_total / 1e9
+    value = replica_throughput(nbytes, K, world, t_total)
     ms_step = t_total / K * 1e3
 
     # end to end through the host-buffer entry point: H2D of row_ptr, col,
@@ -348,10 +363,7 @@ def run_ours(args):
                                           opts=plain, dev_buffer=buf, stream=stream),
                     "ssspmv_csr_f64_host")
         te = (time.perf_counter() - tt0) / args.e2e_steps
-        if world > 1:
-            tt = torch.tensor([te], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
+        te = max_over_ranks(te, dev)
         assert np.array_equal(h_y.numpy(), y.cpu().numpy())
         h2d = (A.m + 1) * 4 + A.nnz * 4 + A.nnz * 8 + A.n * 8
         e2e = {"value": round(nbytes * world / te / 1e9, 3), "unit": "GB/s",
