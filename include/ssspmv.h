@@ -304,14 +304,20 @@ int ssspmv_mlp_select(const float *params, const float *X, int32_t B, int32_t F,
  * SSSPMV_NOALLOC_SCRATCH_BYTES owned by the library, held by every GPU that
  * loads the library until the process exits.  Problems whose
  * ssspmv_workspace_bytes(m, nnz, 8, opts) exceeds it are rejected with
- * SSSPMV_ETOOLARGE before anything runs (8 MiB covers about 950,000 tiles
- * with the automatic bunch count, e.g. nnz up to ~450M at W = 15).
- * All calls on a device share the array and it keeps the last call's
- * contents (the kernels rewrite every entry they read, so nothing needs
- * clearing); calls that overlap on the GPU race on it -- order them on one
- * stream.  The first call on a device looks up the array's address
- * (cudaGetSymbolAddress) with that device current; make it before any stream
- * capture begins.  No call allocates device memory. */
+ * SSSPMV_ETOOLARGE before anything runs (8 MiB covers about 599,000 tiles
+ * with the automatic bunch count -- 8 bytes of tile data per tile plus 24
+ * bytes of synchronizer record per bunch of 4 -- i.e. nnz up to 287,569,920
+ * at W = 15); options the other calls reject are rejected with the same
+ * code.  All calls on a device share the array and it keeps the last call's
+ * contents: each call clears its 16-byte header (error word, bunch ticket,
+ * schedule flag) with cudaMemsetAsync on `stream`, and the kernels write
+ * every other entry before reading it.  Calls that overlap on the GPU race
+ * on the array -- order them on one stream.  The first call on a device
+ * looks up the array's address (cudaGetSymbolAddress) with that device
+ * current and caches it; make it before any stream capture begins.
+ * `stream` must belong to the current device (else SSSPMV_EINVAL).  A
+ * cudaDeviceReset invalidates the cached address: do not call this entry
+ * point again in that process.  No call allocates device memory. */
 #define SSSPMV_NOALLOC_SCRATCH_BYTES (8u << 20)
 int ssspmv_csr_f64_noalloc(int32_t m, int32_t n, int32_t nnz,
                            const int32_t *row_ptr, const int32_t *col_idx, const double *val,

@@ -157,8 +157,8 @@ static cudaEvent_t *timer_next_slot(ssspmv_timer *t)
     return t->ev + 4 * (t->used++);
 }
 
-static int check_csr_args(int32_t m, int32_t n, int32_t nnz, const void *row_ptr,
-                          const void *col, const void *val, const void *x, const void *y)
+int check_csr_args(int32_t m, int32_t n, int32_t nnz, const void *row_ptr, const void *col,
+                   const void *val, const void *x, const void *y)
 {
     if (m < 0 || n < 0 || nnz < 0) return SSSPMV_EINVAL;
     if (m == 0 && nnz != 0) return SSSPMV_EINVAL;

@@ -40,6 +40,7 @@ def _mixed_batch():
     mats.append((E, synth.sym_vector(10, seed=14)))                      # no entries at all
     Z = synth.CSR(0, 0, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
     mats.append((Z, np.zeros(0)))                                        # no rows
+    mats.append(absorbing_row())                                         # 1 + 2^20 * 2^-25
     return mats
 
 
@@ -76,6 +77,16 @@ class Batch:
         return ws
 
 
+def absorbing_row():
+    """One row of 1.0 then 2^20 entries of 2^-25 on column 0 (x = 1): its
+    exact sum 1 + 2^-5 is returned only by compensated accumulation."""
+    n_small = 1 << 20
+    val = np.full(n_small + 1, 2.0 ** -25)
+    val[0] = 1.0
+    rp = np.array([0, n_small + 1], np.int32)
+    return synth.CSR(1, 1, rp, np.zeros(val.size, np.int32), val), np.ones(1)
+
+
 def _single_f32(i, b, opts):
     C = _C()
     A, _ = b.mats[i]
@@ -94,8 +105,8 @@ def _check_all(b, opts, skip=()):
         y = b.y[i].cpu().numpy()
         assert np.array_equal(y, _single_f32(i, b, opts)), "matrix %d differs from the single call" % i
         yref, s = oracle.spmv_dot2(A.row_ptr, A.col, b.v64[i], b.x64[i])
-        n = np.diff(A.row_ptr).astype(np.float64)
-        bound = 2 * U32 * np.abs(yref) + 8 * (n * U32) ** 2 * s
+        # the compensated bound of the reduced-precision tests, rows of any length
+        bound = 2 * U32 * np.abs(yref) + 2 * U32 * s
         y64 = y.astype(np.float64)
         assert np.all(np.abs(y64 - yref) <= bound), "matrix %d outside the bound" % i
         assert np.all(y64[s == 0] == 0.0)
@@ -109,6 +120,8 @@ def test_batch_matches_single_calls(dev, W, S, variant):
     ws = b.run(opts)
     assert C.ssspmv_device_status(ws) == 0
     _check_all(b, opts)
+    # the absorbing row (last matrix) is summed exactly, as in the single call
+    assert abs(float(b.y[-1].cpu()[0]) - (1.0 + 2.0 ** -5)) <= 2 * 2.0 ** -23
 
 
 def test_invalid_descriptor_is_skipped(dev):

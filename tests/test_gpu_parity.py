@@ -314,3 +314,109 @@ def test_stage_timer(dev):
         assert C.ssspmv_timer_read(timer, 8) == []
     finally:
         C.ssspmv_timer_destroy(timer)
+
+
+# ---------------------------------------------------------------------------
+# the speculative stage's own output, before calibration (Sec. 3.2, Alg. 1)
+
+def expected_speculative_rows(row_ptr, col, val, x, L, W, S, info):
+    """Rows kernel (b) stores before calibration and the value each must hold,
+    from the oracle's simulation of the speculative stage (Algorithm 1).
+
+    Kernel (b) stores segment s of tile t at y[tile_offset[t] + s] -- on a
+    dirty tile that is the paper's speculative, misplaced slot -- except:
+    the bunch's first segment goes to the synchronizer record, and a tile's
+    last segment whose row continues into the next tile is carried (the
+    transmitter) and stored by the tile that finishes it.  Tiles resolved in
+    kernel (b) (info bit 30) store every row of (start, stop) at its true
+    row instead.  The oracle follows Algorithm 1, which resets the
+    transmitter after a dirty tile (its checking stage adds that partial back
+    when it moves it); kernel (b) carries it on, so a segment finished after
+    a dirty tile holds the oracle's value plus the dirty tile's last partial,
+    which the oracle leaves in that tile's last speculative slot."""
+    rp = np.asarray(row_ptr, np.int64)
+    m = len(rp) - 1
+    nnz = int(rp[-1])
+    toff = oracle.tile_offsets(row_ptr, L)
+    _, nseg = oracle.tile_flags(row_ptr, L, toff)
+    dirty = oracle.tile_flags(row_ptr, L, toff)[0]
+    st = oracle.speculative_stage(row_ptr, col, val, x, 32, W, S)
+    ys = st["y"]
+    yfin = oracle.spmv(row_ptr, col, val, x)
+    nt = len(nseg)
+    rows, vals = [], []
+    for t0 in range(0, nt, S):
+        t1 = min(t0 + S, nt)
+        rF = int(toff[t0])
+        pending = 0.0   # a dirty tile's carried partial the oracle dropped
+        for t in range(t0, t1):
+            start, stop = int(toff[t]), int(toff[t + 1])
+            e = min((t + 1) * L, nnz)
+            cont = stop < m and rp[stop] < e
+            ns = int(nseg[t])
+            resolved = (int(info[t]) >> 30) & 1
+            carried_on = ns == 1 and cont      # the tile lies inside one row
+            if start != rF and not carried_on:
+                rows.append(start)
+                vals.append(ys[start] + pending)
+            if not carried_on:
+                pending = 0.0
+            if resolved:
+                for r in range(start + 1, stop):
+                    rows.append(r)
+                    vals.append(yfin[r])
+            else:
+                last = ns - 1 if cont else ns
+                for s in range(1, last):
+                    rows.append(start + s)
+                    vals.append(ys[start + s])
+            if cont and dirty[t]:
+                pending += ys[start + ns - 1]
+    return np.asarray(rows, np.int64), np.asarray(vals)
+
+
+def _small_int_case(lens, n, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rp = np.zeros(len(lens) + 1, np.int32)
+    np.cumsum(lens, out=rp[1:])
+    nnz = int(rp[-1])
+    col = rng.integers(0, n, size=nnz).astype(np.int32)
+    val = rng.integers(-8, 9, size=nnz).astype(float)
+    x = rng.integers(-8, 9, size=n).astype(float)
+    return rp, col, val, x
+
+
+@pytest.mark.parametrize("lens", [
+    list(np.random.default_rng(1).integers(0, 70, size=5000)),      # short rows, some empty
+    [3] + [0] * 500 + [4] + [0] * 100 + [2] * 3 + [0] * 70,         # tiles over hundreds of rows
+    ([2] * 240 + [0] * 1500) * 6 + [7] * 50,                         # long dirty tiles
+    [0] * 40 + [900] + [1, 0, 2, 0, 0, 5] * 200 + [1500] + [0, 3] * 300,  # dirty, then a long row
+    [27] * 1000 + [0] + [27] * 1000,                                 # one empty row
+])
+def test_speculative_placement_before_calibration(dev, lens):
+    """y after kernel (b), before kernel (c), slot by slot against the oracle's
+    simulated speculative stage, bit for bit (small integers: every sum is
+    exact in any order): on clean tiles segment s sits in row start + s, on
+    dirty tiles the partials of the next non-empty rows sit in slots
+    start + 1, ... (the paper's misplaced entries of Sec. 3.2), and kernel
+    (b) writes no other row."""
+    rp, col, val, x = _small_int_case(lens, 300, seed=len(lens))
+    api, C = _api()
+    A = api.to_device(rp, col, val, 300, dev)
+    xd = torch.as_tensor(x, dtype=torch.float64, device=dev)
+    for W in (15, 27):
+        for S in (1, 2, 4):
+            for variant in (C.VARIANT_SPECULATIVE, C.VARIANT_EXACT):
+                out = api.spmv_f64_debug(A, xd, C.make_opts(W=W, S=S, variant=variant))
+                L = out["shape"]["L"]
+                rows, want = expected_speculative_rows(rp, col, val, x, L, W, S,
+                                                       out["tile_info"])
+                ys = out["y_spec"]
+                written = np.zeros(len(rp) - 1, bool)
+                written[rows] = True
+                if variant == C.VARIANT_SPECULATIVE:
+                    # kernel (b) writes exactly these rows (y started as NaN)
+                    assert np.array_equal(~np.isnan(ys), written), (W, S, variant)
+                bad = np.nonzero(ys[rows] != want)[0]
+                assert bad.size == 0, (W, S, variant, rows[bad[:5]], ys[rows[bad[:5]]],
+                                       want[bad[:5]])

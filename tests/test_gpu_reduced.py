@@ -3,12 +3,18 @@
 ssspmv_csr_f32 (FP32 val, x, y) and ssspmv_csr_bf16f32 (BF16 val, FP32 x, y)
 accumulate each segment as a compensated FP32 pair (TwoProduct + TwoSum).
 Their error is checked against the FP64 oracle run on the rounded inputs,
-which isolates accumulation error: the bound asserted is that of a
-compensated dot product (Ogita-Rump-Oishi, Prop. 5.5) in single precision
-plus the final rounding to FP32,
-    |y_i - yref_i| <= 2 u |yref_i| + 8 (n_i u)^2 s_i,   u = 2^-24,
-with n_i the row length and s_i = sum_k |a_ik x_k|.  The error against the
-oracle on the original FP64 inputs (input rounding included) is printed.
+which isolates accumulation error.  A compensated sum is as accurate as a
+sum in twice the working precision rounded once (Ogita-Rump-Oishi 2005):
+to first order its error is u |y| + n u^2 s, with n the row length and
+s_i = sum_k |a_ik x_k|, and n u^2 <= u for every row here (n <= 2^24).  The
+tests assert, on rows of every length,
+    |y_i - yref_i| <= 2 u |yref_i| + 2 u s_i,   u = 2^-24,
+which a plain FP32 running sum misses on long rows (its error grows like
+sqrt(n) u s to n u s), and one row built so that only compensation gives
+the exact sum: 1.0 followed by 2^20 entries of 2^-25, x = 1, whose sum
+1 + 2^-5 is an FP32 number (each 2^-25 is below half an ulp of 1, so a
+plain FP32 sum stays near 1).  The error against the oracle on the original
+FP64 inputs (input rounding included) is printed.
 """
 import numpy as np
 import pytest
@@ -20,6 +26,25 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 U32 = 2.0 ** -24
+
+
+def comp_bound(yref, s):
+    """Error bound of the compensated FP32 products on rows of any length."""
+    return 2 * U32 * np.abs(yref) + 2 * U32 * s
+
+
+def absorbing_row(lead_pos: int = 0, m_extra: int = 2):
+    """CSR with one row of 1.0 (at position lead_pos) and 2^20 entries of
+    2^-25, all on column 0 (x = 1), plus m_extra short rows after it; the
+    long row's exact sum is 1 + 2^-5."""
+    n_small = 1 << 20
+    vals = np.full(n_small + 1, 2.0 ** -25)
+    vals[lead_pos] = 1.0
+    extra = np.array([0.5, -0.25] * m_extra)[:m_extra]
+    val = np.concatenate([vals, extra])
+    rp = np.array([0, n_small + 1] + [n_small + 2 + i for i in range(m_extra)], np.int32)
+    col = np.zeros(val.size, np.int32)
+    return synth.CSR(len(rp) - 1, 1, rp, col, val), np.ones(1)
 
 
 @pytest.fixture(scope="module")
@@ -49,8 +74,7 @@ def _run(dev, A, val_dev, x_dev, kind, W=0, S=0):
 
 def _check(A, x64, val_r, x_r, y, label):
     yref, s = oracle.spmv_dot2(A.row_ptr, A.col, val_r, x_r)
-    n = np.diff(A.row_ptr).astype(np.float64)
-    bound = 2 * U32 * np.abs(yref) + 8 * (n * U32) ** 2 * s
+    bound = comp_bound(yref, s)
     err = np.abs(y - yref)
     bad = np.nonzero(~(err <= bound))[0]
     assert bad.size == 0, "%s rows %s err %s bound %s" % (label, bad[:5], err[bad[:5]], bound[bad[:5]])
@@ -115,3 +139,26 @@ def test_rmat22_all_precisions(dev):
     vbf = torch.as_tensor(A.val).to(torch.bfloat16)
     y = _run(dev, A, vbf.to(dev).view(torch.int16), torch.as_tensor(x32, device=dev), "bf16")
     _check(A, x, vbf.to(torch.float64).numpy(), x32.astype(np.float64), y, "bf16 rmat22")
+
+
+EXACT_LONG_ROW = 1.0 + 2.0 ** -5
+
+
+@pytest.mark.parametrize("lead_pos", [0, 7, 480 * 3 + 17])
+def test_compensation_is_exact_on_an_absorbing_row(dev, lead_pos):
+    """Only compensated accumulation returns 1 + 2^-5 for the row of 1.0 and
+    2^20 entries of 2^-25 (within two FP32 ulps of 1; a plain FP32 sum loses
+    hundreds of ulps), in FP32 and BF16-valued storage, for several tile
+    shapes and bunch sizes."""
+    A, x = absorbing_row(lead_pos)
+    x32 = x.astype(np.float32)
+    for kind in ("f32", "bf16"):
+        if kind == "f32":
+            vdev = torch.as_tensor(A.val.astype(np.float32), device=dev)
+        else:
+            vdev = torch.as_tensor(A.val).to(torch.bfloat16).to(dev).view(torch.int16)
+        for W in (15, 27):
+            for S in (0, 1, 3):
+                y = _run(dev, A, vdev, torch.as_tensor(x32, device=dev), kind, W, S)
+                assert abs(y[0] - EXACT_LONG_ROW) <= 2 * 2.0 ** -23, (kind, W, S, y[0])
+                assert np.array_equal(y[1:], A.val[-2:])

@@ -91,3 +91,37 @@ def test_trained_selector_beats_the_fixed_default(dev):
                                     rep["geomean_speedup_oracle_choice_vs_default"]))
     assert rep["mean_regret"] < rep["default_mean_regret"]
     assert rep["geomean_speedup_vs_default"] > 1.0
+
+
+def test_adam_kernel_over_several_steps_with_decay(dev):
+    """ssspmv_mlp_adam against the oracle's Adam for steps t = 1..6 with L2
+    decay, carrying the moments from step to step (the bias corrections at
+    t > 1 and the decay term are exercised, not only the first step)."""
+    from paper_1504_06474_gb300 import ssspmv as C
+    rng = np.random.default_rng(21)
+    n = 1000
+    p = rng.normal(0, 1, n).astype(np.float32)
+    grads = rng.normal(0, 0.5, (6, n)).astype(np.float32)
+    pd = torch.as_tensor(p, device=dev)
+    m1d = torch.zeros(n, dtype=torch.float32, device=dev)
+    m2d = torch.zeros(n, dtype=torch.float32, device=dev)
+    ref_p = p.astype(np.float64)
+    ref_m1 = np.zeros(n)
+    ref_m2 = np.zeros(n)
+    lr, wd = 3e-2, 5e-2
+    for t in range(1, 7):
+        gd = torch.as_tensor(grads[t - 1], device=dev)
+        C.check(C.ssspmv_mlp_adam(pd, gd, m1d, m2d, n, lr, 0.9, 0.999, 1e-8, wd, t), "adam")
+        ref_p, ref_m1, ref_m2 = O.adam_step(ref_p, grads[t - 1].astype(np.float64), ref_m1,
+                                            ref_m2, lr, wd=wd, t=t)
+        # FP32 kernel against the FP64 oracle: a few FP32 roundings per step
+        assert np.allclose(m1d.cpu().numpy(), ref_m1, rtol=1e-5, atol=1e-7), t
+        assert np.allclose(m2d.cpu().numpy(), ref_m2, rtol=1e-5, atol=1e-9), t
+        assert np.allclose(pd.cpu().numpy(), ref_p, rtol=1e-5, atol=1e-6), t
+    # the decay changed the result (the same steps without it land elsewhere)
+    q = p.astype(np.float64)
+    a = np.zeros(n)
+    b = np.zeros(n)
+    for t in range(1, 7):
+        q, a, b = O.adam_step(q, grads[t - 1].astype(np.float64), a, b, lr, wd=0.0, t=t)
+    assert np.max(np.abs(q - ref_p)) > 1e-4

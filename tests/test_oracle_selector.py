@@ -77,3 +77,75 @@ def test_first_adam_step():
     q, m1, m2 = O.adam_step(p, g, np.zeros(3), np.zeros(3), lr=0.01, t=1)
     assert np.allclose(q, p - 0.01 * g / (np.abs(g) + 1e-8))
     assert np.allclose(m1, 0.1 * g) and np.allclose(m2, 0.001 * g * g)
+
+
+def test_adam_hand_worked_three_steps_with_decay():
+    """Kingma & Ba, Algorithm 1, with the L2 decay wd*p added to the gradient,
+    worked by hand for beta1 = 1/2, beta2 = 3/4, lr = 1, eps = 0, wd = 1/2 on
+    two parameters whose raw gradients are constant (1 and -3).
+
+    Parameter A, p = 2:
+      t=1: g = 1 + 2/2 = 2; m = 1; v = 1; mhat = 1/(1-1/2) = 2;
+           vhat = 1/(1-3/4) = 4; p = 2 - 2/2 = 1
+      t=2: g = 1 + 1/2 = 3/2; m = 1/2 + 3/4 = 5/4; v = 3/4 + 9/16 = 21/16;
+           mhat = (5/4)/(1-1/4) = 5/3; vhat = (21/16)/(1-9/16) = 3;
+           p = 1 - 5/(3 sqrt 3)
+      t=3: bias corrections 1 - 1/8 = 7/8 and 1 - 27/64 = 37/64
+    Parameter B, p = -1:
+      t=1: g = -3 - 1/2 = -7/2; m = -7/4; v = 49/16; mhat = -7/2; vhat = 49/4;
+           p = -1 + 1 = 0
+      t=2: g = -3; m = -7/8 - 3/2 = -19/8; v = 147/64 + 9/4 = 291/64;
+           mhat = -19/6; vhat = 291/28; p = (19/6) / sqrt(291/28)
+    """
+    import math
+    p = np.array([2.0, -1.0])
+    graw = np.array([1.0, -3.0])
+    m1 = np.zeros(2)
+    m2 = np.zeros(2)
+    kw = dict(lr=1.0, b1=0.5, b2=0.75, eps=0.0, wd=0.5)
+    p, m1, m2 = O.adam_step(p, graw, m1, m2, t=1, **kw)
+    assert np.array_equal(p, [1.0, 0.0])
+    assert np.array_equal(m1, [1.0, -1.75]) and np.array_equal(m2, [1.0, 49 / 16])
+    p, m1, m2 = O.adam_step(p, graw, m1, m2, t=2, **kw)
+    pA2 = 1 - 5 / (3 * math.sqrt(3))
+    pB2 = (19 / 6) / math.sqrt(291 / 28)
+    assert np.allclose(p, [pA2, pB2], rtol=0, atol=1e-15)
+    assert np.array_equal(m1, [1.25, -19 / 8]) and np.allclose(m2, [21 / 16, 291 / 64], rtol=1e-15)
+    p, m1, m2 = O.adam_step(p, graw, m1, m2, t=3, **kw)
+    # t = 3 by hand from the t = 2 moments
+    gA, gB = 1 + pA2 / 2, -3 + pB2 / 2
+    mA, mB = 5 / 8 + gA / 2, -19 / 16 + gB / 2
+    vA, vB = 63 / 64 + gA * gA / 4, 873 / 256 + gB * gB / 4
+    want = [pA2 - (mA / (7 / 8)) / math.sqrt(vA / (37 / 64)),
+            pB2 - (mB / (7 / 8)) / math.sqrt(vB / (37 / 64))]
+    assert np.allclose(p, want, rtol=0, atol=1e-14)
+    assert abs(p[0] - (-0.8461244626965501)) < 1e-12
+
+
+def test_adam_bias_correction_at_every_step():
+    """With a constant gradient g and no decay, m_t = (1 - b1^t) g and
+    v_t = (1 - b2^t) g^2, so the corrected moments are g and g^2 exactly and
+    every step -- not only the first -- moves by lr * g / (|g| + eps)."""
+    g = np.array([0.25, -4.0, 1e-3])
+    p = np.array([1.0, 2.0, -3.0])
+    m1 = np.zeros(3)
+    m2 = np.zeros(3)
+    for t in range(1, 11):
+        q, m1, m2 = O.adam_step(p, g, m1, m2, lr=0.01, t=t)
+        assert np.allclose(m1, (1 - 0.9 ** t) * g, rtol=1e-12)
+        assert np.allclose(m2, (1 - 0.999 ** t) * g * g, rtol=1e-12)
+        assert np.allclose(q - p, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-9)
+        p = q
+
+
+def test_adam_decay_is_added_to_the_gradient():
+    """L2 decay enters the moments (coupled, as in the paper's Algorithm 1 with
+    the penalty in the objective): with a zero raw gradient the first step is
+    an ordinary Adam step on wd*p and moves p by lr*sign(p) when eps = 0.  A
+    decoupled decay (p -= lr*wd*p beside the Adam step) would move it by
+    lr*wd*|p| instead."""
+    p = np.array([3.0, -0.5])
+    q, m1, m2 = O.adam_step(p, np.zeros(2), np.zeros(2), np.zeros(2), lr=0.1, eps=0.0, wd=0.2,
+                            t=1)
+    assert np.allclose(q, [2.9, -0.4], rtol=0, atol=1e-15)
+    assert np.allclose(m1, 0.1 * 0.2 * p) and np.allclose(m2, 0.001 * (0.2 * p) ** 2)

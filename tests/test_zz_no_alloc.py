@@ -34,6 +34,34 @@ def test_rejects_problems_beyond_the_fixed_scratch(lib):
     assert C.ssspmv_csr_f64_noalloc(-1, 4, 0, FAKE, FAKE, FAKE, FAKE, FAKE) == C.SSSPMV_EINVAL
 
 
+# the largest nnz whose workspace fits the fixed scratch with the default
+# options (W = 15, 4 tiles per bunch): 8 bytes per tile plus a 24-byte
+# synchronizer record per bunch, each section 256-byte aligned
+NOALLOC_MAX_NNZ = 287_569_920
+
+
+def test_capacity_boundary(lib):
+    cap = C.SSSPMV_NOALLOC_SCRATCH_BYTES
+    assert C.ssspmv_workspace_bytes(4_000_000, NOALLOC_MAX_NNZ, 8, None) <= cap
+    assert C.ssspmv_workspace_bytes(4_000_000, NOALLOC_MAX_NNZ + 1, 8, None) > cap
+    # one entry more is rejected on the host, before any device work
+    rc = C.ssspmv_csr_f64_noalloc(4_000_000, 4_000_000, NOALLOC_MAX_NNZ + 1, FAKE, FAKE, FAKE,
+                                  FAKE, FAKE)
+    assert rc == C.SSSPMV_ETOOLARGE
+
+
+def test_same_option_verdicts_as_the_workspace_call(lib):
+    # a tile shape that is not compiled in: EUNSUPPORTED, as ssspmv_csr_f64 says
+    opts = C.make_opts(W=17)
+    assert C.ssspmv_csr_f64_noalloc(100, 100, 1000, FAKE, FAKE, FAKE, FAKE, FAKE,
+                                    opts=opts) == C.SSSPMV_EUNSUPPORTED
+    assert C.ssspmv_csr_f64(100, 100, 1000, FAKE, FAKE, FAKE, FAKE, FAKE, opts=opts,
+                            workspace=FAKE, ws_bytes=1 << 30) == C.SSSPMV_EUNSUPPORTED
+    # a misaligned value array: EINVAL, nothing queued
+    assert C.ssspmv_csr_f64_noalloc(100, 100, 1000, FAKE, FAKE, FAKE + 8, FAKE,
+                                    FAKE) == C.SSSPMV_EINVAL
+
+
 @pytest.mark.gpu
 def test_matches_workspace_entry_point_on_consecutive_calls(lib):
     torch = pytest.importorskip("torch")
