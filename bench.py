@@ -421,6 +421,14 @@ def run_ours(args):
             "gpu_launches": (1 if rows_variant else 3) * K,
             "cpu_baseline": cpu,
         }
+        if world == 1 and args.configs and args.workload == "stencil160" and not args.select:
+            # the other configurations, each with its own clock sample (their
+            # kernels run after the headline's timed region)
+            del Ad, xd, y, ws
+            if "buf" in locals():
+                del buf
+            torch.cuda.empty_cache()
+            line["configs"] = extra_configs(args, dev)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -493,131 +501,311 @@ def _cpu_baseline(mats, budget_s, bytes_of):
     return nbytes / dt / 1e9, used, done, dt
 
 
-def run_precision(args):
+class _Single:
+    """One matrix on the device in one precision: FP64 (val, x, y double),
+    FP32 (val, x, y float) or BF16 values with FP32 x and y."""
+    VB = {"f64": 8, "f32": 4, "bf16": 2}
+
+    def __init__(self, A, x, dev, precision: str):
+        import numpy as np
+        import torch
+        from paper_1504_06474_gb300 import ssspmv as C
+        self.A, self.dev, self.precision = A, dev, precision
+        self.vb = self.VB[precision]
+        self.rp = torch.as_tensor(A.row_ptr, device=dev)
+        self.col = torch.as_tensor(A.col, device=dev)
+        if precision == "f64":
+            self.val = torch.as_tensor(A.val, device=dev)
+            self.x = torch.as_tensor(x, device=dev)
+            self.fn = C.ssspmv_csr_f64
+        elif precision == "f32":
+            self.val = torch.as_tensor(A.val.astype(np.float32), device=dev)
+            self.x = torch.as_tensor(x.astype(np.float32), device=dev)
+            self.fn = C.ssspmv_csr_f32
+        else:
+            self.val = torch.as_tensor(A.val).to(torch.bfloat16).to(dev).view(torch.int16)
+            self.x = torch.as_tensor(x.astype(np.float32), device=dev)
+            self.fn = C.ssspmv_csr_bf16f32
+        ydt = torch.float64 if precision == "f64" else torch.float32
+        self.y = torch.empty(A.m, dtype=ydt, device=dev)
+        self.yb = 8 if precision == "f64" else 4
+        self.nbytes = algorithmic_bytes(A.m, A.n, A.nnz, val_bytes=self.vb, y_bytes=self.yb,
+                                        x_bytes=self.yb)
+
+    def workspace(self, opts):
+        import torch
+        from paper_1504_06474_gb300 import ssspmv as C
+        return torch.empty(max(C.ssspmv_workspace_bytes(self.A.m, self.A.nnz, self.vb, opts), 256),
+                           dtype=torch.uint8, device=self.dev)
+
+    def call(self, opts, ws, stream):
+        from paper_1504_06474_gb300 import ssspmv as C
+        A = self.A
+        C.check(self.fn(A.m, A.n, A.nnz, self.rp, self.col, self.val, self.x, self.y, opts=opts,
+                        workspace=ws, stream=stream), "ssspmv_csr_" + self.precision)
+
+    def rounded_inputs(self):
+        """The values and x as the device stores them, in FP64 (host)."""
+        import numpy as np
+        import torch
+        if self.precision == "f64":
+            return self.A.val, self.x.cpu().numpy()
+        if self.precision == "f32":
+            v = self.val.cpu().numpy().astype(np.float64)
+        else:
+            v = self.val.view(torch.bfloat16).to(torch.float64).cpu().numpy()
+        return v, self.x.cpu().numpy().astype(np.float64)
+
+
+def _time_whole(step, K, flush_l2, stream, gpu, warmup=3):
+    """Mean and median whole-call time (ms) over K flushed steps timed by
+    events around each call, with a clock sample during the timed region."""
+    import torch
+    for _ in range(warmup):
+        flush_l2()
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu)
+    sampler.start()
+    time.sleep(0.25)
+    t = _event_loop(step, flush_l2, K, stream)
+    clocks = sampler.stop()
+    return sum(t) / K, statistics.median(t), clocks
+
+
+def _stages(single, opts_kw, ws, K, flush_l2, stream):
+    """Kernel (a), (b), (c) and whole times (ms) from the library's events
+    at the kernel boundaries, in a run of their own."""
+    from paper_1504_06474_gb300 import ssspmv as C
+    timer = C.ssspmv_timer_create(K)
+    ot = C.make_opts(timer=timer, **opts_kw)
+    _timed_loop(lambda: single.call(ot, ws, stream), flush_l2, K, stream)
+    t = C.ssspmv_timer_read(timer, K)
+    C.ssspmv_timer_destroy(timer)
+    return {"partition": round(sum(v[0] for v in t) / K, 5),
+            "segsum": round(sum(v[1] for v in t) / K, 5),
+            "calibrate": round(sum(v[2] for v in t) / K, 5), "steps": K,
+            "whole": round(sum(v[3] for v in t) / K, 5)}
+
+
+def _errors(single, x64):
+    """Largest |y - yref| / s over rows with s > 0 (s = sum |a x|), against
+    the FP64 oracle on the stored (rounded) inputs and on the FP64 inputs."""
     import numpy as np
+
+    import oracle
+    A = single.A
+    y = single.y.cpu().numpy().astype(np.float64)
+    out = {}
+    v_r, x_r = single.rounded_inputs()
+    yref, s = oracle.spmv_dot2(A.row_ptr, A.col, v_r, x_r)
+    nz = s > 0
+    out["max_err_over_s_rounded_inputs"] = float(np.max(np.abs(y - yref)[nz] / s[nz])) if nz.any() else 0.0
+    out["empty_rows_exact_zero"] = bool(np.all(y[~nz] == 0.0))
+    if single.precision != "f64":
+        y64, s64 = oracle.spmv_dot2(A.row_ptr, A.col, A.val, x64)
+        nz = s64 > 0
+        out["max_err_over_s_fp64_inputs"] = float(np.max(np.abs(y - y64)[nz] / s64[nz])) if nz.any() else 0.0
+    return out
+
+
+def measure_single(A, x, dev, precision, opts_kw, K, workload, cpu_seconds=0.0, e2e_steps=0,
+                   hot=False, compare_f64=True, errors=True):
+    """One configuration of a single product: the JSON line of
+    `--precision` (also used for the configurations of the default run)."""
+    import numpy as np
+    import torch
+    from paper_1504_06474_gb300 import ssspmv as C
+    gpu = dev.index or 0
+    single = _Single(A, x, dev, precision)
+    opts = C.make_opts(**opts_kw)
+    ws = single.workspace(opts)
+    stream = torch.cuda.current_stream(dev)
+    flush = _flusher(dev)
+    flush_l2 = (lambda: None) if hot else flush
+    whole, med, clocks = _time_whole(lambda: single.call(opts, ws, stream), K, flush_l2, stream,
+                                     gpu)
+    st = _stages(single, opts_kw, ws, min(K, 200), flush_l2, stream)
+    nbytes = single.nbytes
+    value = nbytes / (whole / 1e3) / 1e9
+    hbm, peak_kind = peaks()
+    shape = C.ssspmv_plan_shape(A.m, A.nnz, single.vb, opts)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": 1, "steps": K,
+        "warmup": 3, "ms_per_step": round(whole, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f64": "f64", "f32": "f32", "bf16": "bf16-val/f32"}[precision],
+        "data": "synthetic",
+        "config": {"workload": workload, "precision": precision, "m": A.m, "n": A.n,
+                   "nnz": A.nnz, "W": shape["W"], "S": shape["S"], "bytes_per_step": nbytes,
+                   "hbm_frac": round(value / hbm, 4), "us_per_call": round(whole * 1e3, 2),
+                   "ms_per_step_median": round(med, 5), "stage_ms": st,
+                   "l2": ("not flushed (hot: inputs stay in L2 between steps)" if hot else
+                          "flushed between steps (512 MB write then read, outside the timed events)")},
+        "roofline": {"bound": "hbm", "kernel": "segsum_kernel",
+                     "achieved": round(nbytes / (st["segsum"] / 1e3) / 1e9, 2), "peak": hbm,
+                     "unit": "GB/s", "frac": round(nbytes / (st["segsum"] / 1e3) / 1e9 / hbm, 4),
+                     "peak_kind": peak_kind, "traffic": None},
+        "clocks": clocks, "gpu_launches": 3 * K,
+    }
+    if precision != "f64":
+        line["config"]["accumulation"] = "compensated FP32 pairs (TwoProduct + TwoSum)"
+    if errors:
+        line["config"]["error"] = _errors(single, x)
+    if compare_f64 and precision != "f64":
+        # the plain FP64 call on the same matrix, same GPU, same timing
+        s64 = _Single(A, x, dev, "f64")
+        ws64 = s64.workspace(None)
+        ms64, _, _ = _time_whole(lambda: s64.call(None, ws64, stream), min(K, 200), flush_l2,
+                                 stream, gpu)
+        line["config"]["plain_f64_ms"] = round(ms64, 5)
+        line["config"]["speedup_vs_plain_f64"] = round(ms64 / whole, 3)
+        del s64, ws64
+    e2e = None
+    if e2e_steps > 0:
+        # pinned host inputs in, y out, every step
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        h = [pin(A.row_ptr), pin(A.col), single.val.cpu().pin_memory(), single.x.cpu().pin_memory()]
+        d = [single.rp, single.col, single.val, single.x]
+        hy = torch.empty(A.m, dtype=single.y.dtype).pin_memory()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            for dst, src in zip(d, h):
+                dst.copy_(src, non_blocking=True)
+            single.call(opts, ws, stream)
+            hy.copy_(single.y, non_blocking=True)
+            torch.cuda.synchronize(dev)
+        te = (time.perf_counter() - t0) / e2e_steps
+        h2d = sum(v.numel() * v.element_size() for v in h)
+        e2e = {"value": round(nbytes / te / 1e9, 3), "unit": "GB/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": A.m * single.yb, "ms_per_step": round(te * 1e3, 4)}
+    line["e2e"] = e2e
+    status = C.ssspmv_device_status(ws, stream=stream)
+    if status:
+        raise RuntimeError("device status bits %#x" % status)
+    cpu = None
+    if cpu_seconds > 0:
+        rate, used, reps, dt = _cpu_baseline([(A, x)], cpu_seconds, lambda M: nbytes)
+        cpu = {"value": round(rate, 3), "unit": "GB/s", "cores": used, "kind": "oracle",
+               "sample": "%d whole %s SpMVs by the FP64 oracle row loop (%d OpenMP threads), "
+                         "counted at this configuration's bytes per step, %.1f s"
+                         % (reps, workload, used, dt)}
+    line["cpu_baseline"] = cpu
+    return line
+
+
+def _select_compare(single, dev, K, flush_l2, gpu):
+    """The shipped selector's class for this FP64 matrix (from its device
+    features) timed beside the default configuration."""
+    import torch
+    from paper_1504_06474_gb300 import selector as SEL
+    from paper_1504_06474_gb300 import ssspmv as C
+    params = SEL.load_default()
+    if params is None:
+        return {"unavailable": "no selector weights shipped with the package"}
+    A = single.A
+    f = SEL.device_features(single.rp, A.m, A.n, A.nnz).cpu().numpy()[None, :]
+    k = int(SEL.select(params, f, dev)[0])
+    kw = SEL.CLASSES[k][1]
+    stream = torch.cuda.current_stream(dev)
+    o_sel = C.make_opts(W=kw.get("W", 0), variant=kw.get("variant", 0),
+                        block_warps=kw.get("block_warps", 0))
+    o_def = C.make_opts()
+    ws_s, ws_d = single.workspace(o_sel), single.workspace(o_def)
+    ms_s, _, clocks = _time_whole(lambda: single.call(o_sel, ws_s, stream), K, flush_l2, stream, gpu)
+    ms_d, _, _ = _time_whole(lambda: single.call(o_def, ws_d, stream), K, flush_l2, stream, gpu)
+    return {"class": SEL.CLASSES[k][0], "index": k, "selected_ms": round(ms_s, 5),
+            "default_ms": round(ms_d, 5), "speedup_vs_default": round(ms_d / ms_s, 4),
+            "clocks": clocks}
+
+
+def _summary(line, keep_error=True):
+    """The fields of a configuration's line that go into the default run's
+    `configs` object."""
+    c = line["config"]
+    out = {"value": line["value"], "unit": line["unit"], "dtype": line["dtype"],
+           "ms_per_step": line["ms_per_step"], "hbm_frac": c.get("hbm_frac"),
+           "kernel_b_frac": line["roofline"]["frac"], "stage_ms": c.get("stage_ms"),
+           "steps": line["steps"], "clocks": line["clocks"], "l2": c.get("l2")}
+    for k in ("us_per_call", "speedup_vs_plain_f64", "plain_f64_ms", "W", "S", "m", "nnz"):
+        if k in c:
+            out[k] = c[k]
+    if keep_error and "error" in c:
+        out["error"] = c["error"]
+    if line.get("cpu_baseline"):
+        out["cpu_baseline"] = line["cpu_baseline"]
+    return out
+
+
+def extra_configs(args, dev):
+    """The other configurations of the benchmark, measured in the same run
+    beside the headline: the small uniform matrix (flushed and hot), the
+    power-law graph in FP64, FP32 and BF16 values (each with its error
+    against the FP64 oracle), the batch of 512 matrices under a CUDA graph,
+    and the shipped selector on the stencil and the power-law graph."""
+    import types
+    import torch
+
+    import synth
+    gpu = dev.index or 0
+    K = args.config_steps
+    out = {}
+    t0 = time.perf_counter()
+    A, x = synth.workload("uniform4096")
+    flushed = measure_single(A, x, dev, "f64", {}, 4 * K, "uniform4096",
+                             cpu_seconds=args.config_cpu_seconds)
+    hot = measure_single(A, x, dev, "f64", {}, 4 * K, "uniform4096", hot=True, errors=False)
+    u = _summary(flushed)
+    u["hot"] = {"us_per_call": hot["config"]["us_per_call"], "value": hot["value"],
+                "stage_ms": hot["config"]["stage_ms"], "clocks": hot["clocks"]}
+    out["uniform4096_f64"] = u
+    A, x = synth.workload("rmat22")
+    for prec in ("f64", "f32", "bf16"):
+        line = measure_single(A, x, dev, prec, {}, K, "rmat22",
+                              cpu_seconds=args.config_cpu_seconds if prec == "f64" else 0.0)
+        out["rmat22_" + prec] = _summary(line)
+        torch.cuda.empty_cache()
+    flush = _flusher(dev)
+    out["select_rmat22"] = _select_compare(_Single(A, x, dev, "f64"), dev, K, flush, gpu)
+    del A, x
+    S, xs = synth.workload("stencil160")
+    out["select_stencil160"] = _select_compare(_Single(S, xs, dev, "f64"), dev, K, flush, gpu)
+    del S, xs
+    torch.cuda.empty_cache()
+    ns = types.SimpleNamespace(workload="batch512", tile_w=0, tile_s=0, variant=0, warmup=3,
+                               steps=max(10, K // 5), e2e_steps=2,
+                               cpu_seconds=args.config_cpu_seconds)
+    b = measure_batch(ns, dev)
+    bs = {"value": b["value"], "unit": b["unit"], "dtype": b["dtype"],
+          "ms_per_step": b["ms_per_step"], "hbm_frac": b["config"]["hbm_frac"],
+          "kernel_b_frac": b["roofline"]["frac"], "steps": b["steps"], "clocks": b["clocks"]}
+    for k in ("matrices", "families", "rows", "nnz", "W", "variant", "autotuned", "launch",
+              "stage_ms", "speedup_vs_separate_f32_calls", "speedup_vs_plain_f64",
+              "separate_f32_calls_ms", "separate_plain_f64_calls_ms", "l2"):
+        bs[k] = b["config"][k]
+    bs["e2e"] = b["e2e"]
+    bs["cpu_baseline"] = b["cpu_baseline"]
+    out["batch512_f32"] = bs
+    torch.cuda.empty_cache()
+    out["wall_s"] = round(time.perf_counter() - t0, 1)
+    return out
+
+
+def run_precision(args):
     import torch
 
     import synth
     from paper_1504_06474_gb300 import _build
-    from paper_1504_06474_gb300 import ssspmv as C
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     _build.build()
     A, x = synth.workload(args.workload)
-    vb = 4 if args.precision == "f32" else 2
-    rp = torch.as_tensor(A.row_ptr, device=dev)
-    col = torch.as_tensor(A.col, device=dev)
-    if vb == 4:
-        val = torch.as_tensor(A.val.astype(np.float32), device=dev)
-        fn = C.ssspmv_csr_f32
-    else:
-        val = torch.as_tensor(A.val).to(torch.bfloat16).to(dev).view(torch.int16)
-        fn = C.ssspmv_csr_bf16f32
-    xd = torch.as_tensor(x.astype(np.float32), device=dev)
-    y = torch.empty(A.m, dtype=torch.float32, device=dev)
-    opts = C.make_opts(W=args.tile_w, S=args.tile_s, variant=args.variant)
-    ws = torch.empty(C.ssspmv_workspace_bytes(A.m, A.nnz, vb, opts), dtype=torch.uint8,
-                     device=dev)
-    stream = torch.cuda.current_stream(dev)
-    flush_l2 = _flusher(dev)
-
-    def step():
-        C.check(fn(A.m, A.n, A.nnz, rp, col, val, xd, y, opts=opts, workspace=ws,
-                   stream=stream), "reduced-precision call")
-    for _ in range(args.warmup):
-        step()
-    K = args.steps
-    sampler = ClockSampler(local)
-    torch.cuda.synchronize(dev)
-    sampler.start()
-    time.sleep(0.25)
-    per_step = _event_loop(step, flush_l2, K, stream)
-    clocks = sampler.stop()
-    whole = sum(per_step) / K
-    # stage breakdown from the library's events, in a run of its own
-    Ks = min(K, 200)
-    timer = C.ssspmv_timer_create(Ks)
-    opts_t = C.make_opts(W=args.tile_w, S=args.tile_s, variant=args.variant, timer=timer)
-
-    def step_t():
-        C.check(fn(A.m, A.n, A.nnz, rp, col, val, xd, y, opts=opts_t, workspace=ws,
-                   stream=stream), "reduced-precision call")
-    _timed_loop(step_t, flush_l2, Ks, stream)
-    t = C.ssspmv_timer_read(timer, Ks)
-    C.ssspmv_timer_destroy(timer)
-    seg = sum(v[1] for v in t) / Ks
-    nbytes = algorithmic_bytes(A.m, A.n, A.nnz, val_bytes=vb, y_bytes=4, x_bytes=4)
-    value = nbytes / (whole / 1e3) / 1e9
-    # the plain FP64 call on the same matrix, same GPU, same timing
-    rp64, col64 = rp, col
-    val64 = torch.as_tensor(A.val, device=dev)
-    x64 = torch.as_tensor(x, device=dev)
-    y64 = torch.empty(A.m, dtype=torch.float64, device=dev)
-    ws64 = torch.empty(C.ssspmv_workspace_bytes(A.m, A.nnz, 8, None), dtype=torch.uint8,
-                       device=dev)
-
-    def step64():
-        C.check(C.ssspmv_csr_f64(A.m, A.n, A.nnz, rp64, col64, val64, x64, y64, workspace=ws64,
-                                 stream=stream), "ssspmv_csr_f64")
-    for _ in range(args.warmup):
-        step64()
-    t64 = _timed_loop(step64, flush_l2, min(K, 200), stream)
-    ms64 = sum(t64) / len(t64)
-    # end to end: pinned host inputs in, y out, every step
-    e2e = None
-    if args.e2e_steps > 0:
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        h = [pin(A.row_ptr), pin(A.col), val.cpu().pin_memory(), pin(x.astype(np.float32))]
-        d = [rp, col, val, xd]
-        hy = torch.empty(A.m, dtype=torch.float32).pin_memory()
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            for dst, src in zip(d, h):
-                dst.copy_(src, non_blocking=True)
-            step()
-            hy.copy_(y, non_blocking=True)
-            torch.cuda.synchronize(dev)
-        te = (time.perf_counter() - t0) / args.e2e_steps
-        h2d = sum(v.numel() * v.element_size() for v in h)
-        e2e = {"value": round(nbytes / te / 1e9, 3), "unit": "GB/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": A.m * 4, "ms_per_step": round(te * 1e3, 4)}
-    status = C.ssspmv_device_status(ws, stream=stream)
-    if status:
-        raise RuntimeError("device status bits %#x" % status)
-    cpu = None
-    if args.cpu_seconds > 0:
-        rate, used, reps, dt = _cpu_baseline([(A, x)], args.cpu_seconds,
-                                             lambda M: nbytes)
-        cpu = {"value": round(rate, 3), "unit": "GB/s", "cores": used, "kind": "oracle",
-               "sample": "%d whole %s SpMVs by the FP64 oracle row loop (%d OpenMP threads), "
-                         "counted at this configuration's bytes per step, %.1f s"
-                         % (reps, args.workload, used, dt)}
-    hbm, peak_kind = peaks()
-    shape = C.ssspmv_plan_shape(A.m, A.nnz, vb, opts)
-    line = {
-        "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": 1, "steps": K,
-        "warmup": args.warmup, "ms_per_step": round(whole, 5), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if vb == 4 else "bf16-val/f32", "data": "synthetic",
-        "config": {"workload": args.workload, "precision": args.precision, "m": A.m,
-                   "n": A.n, "nnz": A.nnz, "W": shape["W"], "S": shape["S"],
-                   "bytes_per_step": nbytes, "hbm_frac": round(value / hbm, 4),
-                   "accumulation": "compensated FP32 pairs (TwoProduct + TwoSum)",
-                   "stage_ms": {"partition": round(sum(v[0] for v in t) / Ks, 5),
-                                "segsum": round(seg, 5),
-                                "calibrate": round(sum(v[2] for v in t) / Ks, 5),
-                                "steps": Ks, "whole": round(sum(v[3] for v in t) / Ks, 5)},
-                   "ms_per_step_median": round(statistics.median(per_step), 5),
-                   "plain_f64_ms": round(ms64, 5), "speedup_vs_plain_f64": round(ms64 / whole, 3),
-                   "l2": "flushed between steps (512 MB write then read, outside the timed events)"},
-        "roofline": {"bound": "hbm", "kernel": "segsum_kernel",
-                     "achieved": round(nbytes / (seg / 1e3) / 1e9, 2), "peak": hbm,
-                     "unit": "GB/s", "frac": round(nbytes / (seg / 1e3) / 1e9 / hbm, 4),
-                     "peak_kind": peak_kind, "traffic": None},
-        "clocks": clocks, "e2e": e2e, "gpu_launches": 3 * K, "cpu_baseline": cpu,
-    }
+    line = measure_single(A, x, dev, args.precision,
+                          dict(W=args.tile_w, S=args.tile_s, variant=args.variant), args.steps,
+                          args.workload, cpu_seconds=args.cpu_seconds,
+                          e2e_steps=args.e2e_steps, hot=args.hot)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -626,16 +814,26 @@ def run_precision(args):
 # a batch of many matrices (FP32) in one graph launch
 
 def run_batch(args):
-    import numpy as np
     import torch
 
-    import synth
     from paper_1504_06474_gb300 import _build
-    from paper_1504_06474_gb300 import ssspmv as C
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     _build.build()
+    print(json.dumps(measure_batch(args, dev)), flush=True)
+    return 0
+
+
+def measure_batch(args, dev):
+    """The batched FP32 call over a seeded mixed batch as one CUDA-graph
+    replay, beside the same matrices as separate calls; returns the line."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1504_06474_gb300 import ssspmv as C
+    local = dev.index or 0
     count = int(args.workload[len("batch"):])
     specs = synth.batch_specs(count, seed=3)
     t_gen = time.perf_counter()
@@ -783,8 +981,7 @@ def run_batch(args):
                      "peak_kind": peak_kind, "traffic": None},
         "clocks": clocks, "e2e": e2e, "gpu_launches": 4 * K, "cpu_baseline": cpu,
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def main():
@@ -806,6 +1003,14 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--hot", action="store_true",
                     help="no L2 flush between steps (for workloads that fit in L2, e.g. uniform4096)")
+    ap.add_argument("--configs", action=argparse.BooleanOptionalAction, default=True,
+                    help="after the stencil160 FP64 headline, measure the other configurations "
+                         "(uniform4096, rmat22 FP64/FP32/BF16, batch512, the selector) into the "
+                         "line's `configs` object")
+    ap.add_argument("--config-steps", type=int, default=100,
+                    help="timed steps per configuration of `configs`")
+    ap.add_argument("--config-cpu-seconds", type=float, default=3.0,
+                    help="CPU-oracle budget per configuration of `configs`")
     ap.add_argument("--precision", choices=["f64", "f32", "bf16"], default="f64",
                     help="f32: FP32 val/x/y; bf16: BF16 val, FP32 x/y (compensated FP32 sums)")
     args = ap.parse_args()

@@ -109,11 +109,15 @@ def test_adam_kernel_over_several_steps_with_decay(dev):
     ref_m1 = np.zeros(n)
     ref_m2 = np.zeros(n)
     lr, wd = 3e-2, 5e-2
+    # the kernel receives the hyperparameters as FP32 numbers (1 - float(0.999)
+    # is 1.3e-5 away from 0.001): the oracle takes the same rounded values
+    f32 = lambda v: float(np.float32(v))
+    hp = dict(b1=f32(0.9), b2=f32(0.999), eps=f32(1e-8), wd=f32(wd))
     for t in range(1, 7):
         gd = torch.as_tensor(grads[t - 1], device=dev)
         C.check(C.ssspmv_mlp_adam(pd, gd, m1d, m2d, n, lr, 0.9, 0.999, 1e-8, wd, t), "adam")
         ref_p, ref_m1, ref_m2 = O.adam_step(ref_p, grads[t - 1].astype(np.float64), ref_m1,
-                                            ref_m2, lr, wd=wd, t=t)
+                                            ref_m2, f32(lr), t=t, **hp)
         # FP32 kernel against the FP64 oracle: a few FP32 roundings per step
         assert np.allclose(m1d.cpu().numpy(), ref_m1, rtol=1e-5, atol=1e-7), t
         assert np.allclose(m2d.cpu().numpy(), ref_m2, rtol=1e-5, atol=1e-9), t
