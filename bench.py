@@ -803,7 +803,8 @@ def run_precision(args):
     _build.build()
     A, x = synth.workload(args.workload)
     line = measure_single(A, x, dev, args.precision,
-                          dict(W=args.tile_w, S=args.tile_s, variant=args.variant), args.steps,
+                          dict(W=args.tile_w, S=args.tile_s, variant=args.variant,
+                               block_warps=args.block_warps), args.steps,
                           args.workload, cpu_seconds=args.cpu_seconds,
                           e2e_steps=args.e2e_steps, hot=args.hot)
     print(json.dumps(line), flush=True)
@@ -861,7 +862,8 @@ def measure_batch(args, dev):
         kw, cand_ms = S.tune_batched(count, desc, total_nnz, dev)
         tuned = {"chosen": kw, "candidates_ms": {k: round(v, 4) for k, v in cand_ms.items()}}
         args.tile_w, args.variant = kw["W"], kw["variant"]
-    opts = C.make_opts(W=args.tile_w, S=args.tile_s, variant=args.variant)
+    bwarps = getattr(args, "block_warps", 0)
+    opts = C.make_opts(W=args.tile_w, S=args.tile_s, variant=args.variant, block_warps=bwarps)
     ws = torch.empty(C.ssspmv_batched_workspace_bytes(count, total_nnz, 4, opts),
                      dtype=torch.uint8, device=dev)
     s = torch.cuda.Stream(dev)
@@ -890,7 +892,8 @@ def measure_batch(args, dev):
     # stage split from direct (uncaptured) launches with the library's timer
     kst = min(K, 20)
     timer = C.ssspmv_timer_create(kst)
-    ot = C.make_opts(W=args.tile_w, S=args.tile_s, variant=args.variant, timer=timer)
+    ot = C.make_opts(W=args.tile_w, S=args.tile_s, variant=args.variant, timer=timer,
+                     block_warps=bwarps)
     with torch.cuda.stream(s):
         _timed_loop(lambda: batched(ot), flush_l2, kst, s)
     st = C.ssspmv_timer_read(timer, kst)

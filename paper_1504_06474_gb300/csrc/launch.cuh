@@ -83,11 +83,12 @@ int segsum_resident_warps(int bw)
 // warps per block of kernel (b).  Automatic choice: every warp that fits in
 // shared memory for long rows; for short rows (mean below 20 entries, where
 // power-law column patterns reuse x heavily) only as many as keep the
-// shared-memory carve-out at or below 200 KB, so about 56 KB of L1 stays
-// for the gathers, and at most the precision's kShortRowWarps.  Measured on
+// shared-memory carve-out at or below 200 KB and at most the precision's
+// kShortRowWarps, so that L1 keeps room for the gathered x.  Measured on
 // W = 15: a 27-point stencil runs 3% faster with all 19 FP64 warps (6% with
-// 24 FP32 warps), an R-MAT graph 30% faster with 17 FP64 warps (10% with 20
-// FP32 warps).
+// 24 FP32 warps); R-MAT scale 22 runs kernel (b) in 359 us with 14 FP64
+// warps against 379 with 17 and 576 with 19, and R-MAT scale 20 in FP32
+// 8% faster with 16 warps than with 20.
 template <class P, int W>
 int segsum_block_warps(const Call &c)
 {

@@ -31,7 +31,7 @@ namespace ssspmv {
 
 struct F64 {
     static constexpr int kMaxWarps = 32;  // shared memory decides
-    static constexpr int kShortRowWarps = 17;  // short rows: keep L1 for the gathers (measured)
+    static constexpr int kShortRowWarps = 14;  // short rows: keep L1 for the gathers (measured)
     using val_t = double;
     using x_t = double;
     using y_t = double;
@@ -87,7 +87,7 @@ struct CompF32Traits {
     // BF16 values need more registers for the widening: 20 (96)
     static constexpr int kMaxWarps = std::is_same<V, float>::value ? 24 : 20;
     static constexpr int kBatchMaxWarps = 20;  // the batched kernel needs more registers
-    static constexpr int kShortRowWarps = 20;  // short rows: keep L1 for the gathers (measured)
+    static constexpr int kShortRowWarps = 16;  // short rows: keep L1 for the gathers (measured)
     using val_t = V;
     using x_t = float;
     using y_t = float;
