@@ -172,11 +172,11 @@ def tune_batched(count: int, desc, total_nnz: int, dev, reps: int = 3):
 # ---------------------------------------------------------------------------
 # the seeded training set: six families, m log-uniform
 
-FAMILIES = ("banded", "stencil", "rmat", "blockdiag", "uniform", "longrows")
+FAMILIES = ("banded", "stencil", "rmat", "blockdiag", "uniform", "longrows", "rmatlong")
 
 
 def dataset_specs(count: int, seed: int, m_lo: int = 10_000, m_hi: int = 8_000_000,
-                  max_nnz: int = 64_000_000):
+                  max_nnz: int = 120_000_000):
     """(family, m, parameter, seed) per matrix; m log-uniform in [m_lo, m_hi]
     and lowered where the family's nnz would pass max_nnz."""
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -199,8 +199,13 @@ def dataset_specs(count: int, seed: int, m_lo: int = 10_000, m_hi: int = 8_000_0
         elif fam == "uniform":
             par = int(rng.integers(2, 41))            # longest row
             m = min(m, max_nnz // par)
-        else:
+        elif fam == "longrows":
             par = int(rng.integers(1, 9))             # number of long rows
+        else:
+            # R-MAT over 2^ceil(log2 m) rows with one injected row of a quarter
+            # of them (the power-law benchmark graph's shape)
+            par = int(rng.integers(4, 17))            # edge factor
+            m = min(m, max_nnz // (par + 1))
         out.append((fam, max(m, 64), par, seed * 1_000_003 + i))
     return out
 
@@ -219,8 +224,11 @@ def make_matrix(spec):
         A = synth.blockdiag(m, 32, par, s)
     elif fam == "uniform":
         A = synth.range_rows(m, 0, par, s)
-    else:
+    elif fam == "longrows":
         A = synth.long_rows(m, par, min(m, 2_000_000), s)
+    else:
+        scale = max(6, int(math.ceil(math.log2(m))))
+        A = synth.rmat(scale, par, seed=s, inject_len=min(1 << (scale - 2), 1_000_000))
     return A, synth.sym_vector(A.n, seed=s)
 
 
