@@ -323,6 +323,60 @@ int ssspmv_csr_f64_noalloc(int32_t m, int32_t n, int32_t nnz,
                            const int32_t *row_ptr, const int32_t *col_idx, const double *val,
                            const double *x, double *y, const ssspmv_opts *opts, void *stream);
 
+/* One product split across devices by tile ranges (not in the paper, which
+ * runs on one processor; the combination is its synchronization step of
+ * Sec. 3.2 and Algorithm 1 one level up, between shards instead of
+ * thread-bunches).  Shard g takes the tiles [t0, t1) of the whole matrix's
+ * tiling (the same opts, hence the same tile length L, on every shard),
+ * i.e. the nonzeros [B, E) = [min(t0 L, nnz), min(t1 L, nnz)).  Its rows
+ * are r_first = the largest r with row_ptr[r] <= B and r_last = the largest r
+ * with row_ptr[r] <= E (m for the shard that ends the matrix):
+ *   - rows strictly between them lie inside [B, E): the shard writes their
+ *     final y (empty rows 0);
+ *   - rows r_first and r_last are cut: the shard writes its partial sums of
+ *     them into y and into `seam`, and the sum over all shards' partials of
+ *     such a row is its y (ssspmv_seam_merge);
+ *   - the shard with t0 = 0 also zeroes the leading empty rows [0, r_first).
+ * Shards share nothing on the device; the seam records (32 bytes each) are
+ * the only exchange.  Their tiles are the unsplit product's tiles, so each
+ * tile's arithmetic is the same as in ssspmv_csr_f64.
+ *   ssspmv_range_bounds   r_first and r_last of [t0, t1) from the device
+ *     row_ptr (a search kernel; allocates 8 bytes stream-ordered and
+ *     synchronises `stream`).  0 <= t0 <= t1 <= ntiles (ssspmv_plan_shape).
+ *   ssspmv_range_workspace_bytes  device workspace of the range call
+ *     (the shard's shifted row pointers plus the workspace of its rows).
+ *   ssspmv_csr_f64_range  the shard's product on `stream`: kernels (a), (b),
+ *     (c) on rows [r_first, r_last] (r_last < m) or [r_first, m), with
+ *     row_ptr shifted by B and clamped to [0, E - B], col_idx and val read
+ *     from entry B on; then `seam` (DEVICE pointer) receives {r_first, its
+ *     partial} and {r_last, its partial} (row -1 where there is no second
+ *     cut row) and status 0, or SSSPMV_DEV_RANGE if r_first/r_last do not
+ *     match row_ptr (then y is not the product).  opts->timer must be NULL;
+ *     ROWS is not supported.  Arrays as for ssspmv_csr_f64 (x whole).
+ *   ssspmv_seam_merge  HOST records of `shards` shards in shard order ->
+ *     the cut rows and their final values (each the sum of that row's
+ *     partials in shard order, so deterministic); rows/vals (host, up to
+ *     2*shards entries, may be NULL to count) and *count.  Returns
+ *     SSSPMV_EDEVICE if a record has a non-zero status, SSSPMV_EINVAL if the
+ *     records are out of order.  The caller then stores vals into y[rows]. */
+typedef struct ssspmv_seam {
+    int32_t row[2];   /* rows cut at the shard's start and end; -1: none */
+    int32_t status;   /* 0, or SSSPMV_DEV_RANGE (bounds do not match row_ptr) */
+    int32_t reserved;
+    double val[2];    /* the shard's partial sums of those rows */
+} ssspmv_seam;        /* 32 bytes */
+int ssspmv_range_bounds(int32_t m, int32_t nnz, const int32_t *row_ptr, const ssspmv_opts *opts,
+                        int64_t t0, int64_t t1, int32_t *r_first, int32_t *r_last, void *stream);
+size_t ssspmv_range_workspace_bytes(int32_t m, int32_t nnz, int64_t t0, int64_t t1,
+                                    int32_t r_first, int32_t r_last, const ssspmv_opts *opts);
+int ssspmv_csr_f64_range(int32_t m, int32_t n, int32_t nnz,
+                         const int32_t *row_ptr, const int32_t *col_idx, const double *val,
+                         const double *x, double *y, int64_t t0, int64_t t1,
+                         int32_t r_first, int32_t r_last, ssspmv_seam *seam,
+                         const ssspmv_opts *opts, void *workspace, size_t ws_bytes, void *stream);
+int ssspmv_seam_merge(int32_t shards, const ssspmv_seam *seams, int32_t *rows, double *vals,
+                      int32_t *count);
+
 /* The same product with HOST arrays (pageable or pinned): copies row_ptr,
  * col_idx, val and x into `dev_buffer` (device memory of at least
  * ssspmv_host_buffer_bytes() bytes), runs ssspmv_csr_f64 on `stream`, copies

@@ -10,6 +10,8 @@ Functions (each cites the passage it follows in ``oracle.c``):
 
 * ``spmv(A, x)``             plain row loop, y = A x (Sec. 2.1)
 * ``spmv_omp(A, x)``         same, rows split over OpenMP threads (Sec. 4.3)
+* ``spmv_range(A, x, B, E)`` the row loop over the nonzeros [B, E) only
+                             (one shard of a product split by ranges)
 * ``spmv_dot2(A, x)``        compensated reference and per-row scale
                              sum_k |a_k x_k| (Ogita-Rump-Oishi Dot2)
 * ``tile_offsets``, ``descriptors``, ``tile_flags``  index artefacts (Sec. 3.2)
@@ -51,6 +53,8 @@ def _load():
         lib.oracle_spmv_rowloop.argtypes = [i32, P, P, P, P, P]
         lib.oracle_spmv_rowloop_omp.restype = ctypes.c_int
         lib.oracle_spmv_rowloop_omp.argtypes = [i32, P, P, P, P, P, ctypes.c_int]
+        lib.oracle_spmv_range.restype = None
+        lib.oracle_spmv_range.argtypes = [i32, P, P, P, P, i64, i64, P]
         lib.oracle_spmv_dot2.restype = None
         lib.oracle_spmv_dot2.argtypes = [i32, P, P, P, P, P, P]
         lib.oracle_num_tiles.restype = i64
@@ -101,6 +105,17 @@ def spmv_omp(row_ptr, col, val, x, nthreads: int = 0, y=None):
     used = _load().oracle_spmv_rowloop_omp(m, _p(row_ptr), _p(col), _p(val), _p(x), _p(y),
                                            nthreads)
     return y, used
+
+
+def spmv_range(row_ptr, col, val, x, B: int, E: int) -> np.ndarray:
+    """The row loop over the nonzeros [B, E) only (Sec. 2.1 restricted to one
+    shard of a product split by entry ranges)."""
+    row_ptr, col, val = _csr(row_ptr, col, val)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    m = len(row_ptr) - 1
+    y = np.empty(m, dtype=np.float64)
+    _load().oracle_spmv_range(m, _p(row_ptr), _p(col), _p(val), _p(x), int(B), int(E), _p(y))
+    return y
 
 
 def spmv_dot2(row_ptr, col, val, x):

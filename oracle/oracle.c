@@ -89,6 +89,24 @@ int oracle_spmv_rowloop_omp(int32_t m, const int32_t *row_ptr, const int32_t *co
     return used;
 }
 
+/* the plain definition restricted to the nonzeros [B, E): y_i = sum of
+ * val_k x[col_k] over k in [row_ptr[i], row_ptr[i+1]) with B <= k < E (a row
+ * with no entries there is 0).  Summing these over a partition of [0, nnz)
+ * into ranges gives the row loop's y; it is what one shard of a product
+ * split by tile ranges contributes to each row. */
+void oracle_spmv_range(int32_t m, const int32_t *row_ptr, const int32_t *col,
+                       const double *val, const double *x, int64_t B, int64_t E, double *y)
+{
+    for (int32_t i = 0; i < m; ++i) {
+        int64_t lo = row_ptr[i] > B ? row_ptr[i] : B;
+        int64_t hi = row_ptr[i + 1] < E ? row_ptr[i + 1] : E;
+        double s = 0.0;
+        for (int64_t k = lo; k < hi; ++k)
+            s += val[k] * x[col[k]];
+        y[i] = s;
+    }
+}
+
 /* Error-free transformations: TwoSum (Knuth, TAOCP vol. 2) and TwoProduct by
  * fused multiply-add; Dot2 is Algorithm 5.3 of Ogita, Rump and Oishi,
  * "Accurate sum and dot product", SIAM J. Sci. Comput. 26 (2005).  The result

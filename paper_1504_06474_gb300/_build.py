@@ -15,7 +15,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libssspmv.so")
 
 SOURCES = ["api.cu", "partition.cu", "spmv_f64.cu", "spmv_f32.cu", "spmv_bf16.cu", "batched.cu",
-           "rows.cu", "mlp.cu", "noalloc.cu"]
+           "rows.cu", "mlp.cu", "noalloc.cu", "range.cu"]
 HEADERS = ["ptx.cuh", "segsum.cuh", "launch.cuh", "layout.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -5,6 +5,8 @@ from __future__ import annotations
 
 from dataclasses import dataclass
 
+import numpy as np
+
 import torch
 
 from . import ssspmv as _c
@@ -71,3 +73,38 @@ def spmv_f64_debug(A: DeviceCSR, x: torch.Tensor, opts=None, stream=None) -> dic
                 desc=desc.cpu().numpy().view("uint32")[: nt * W].reshape(nt, W),
                 tile_info=info.cpu().numpy().view("uint32")[:nt],
                 sync_idx=sidx.cpu().numpy()[:nb], shape=shape)
+
+
+# ---------------------------------------------------------------------------
+# one product split by tile ranges (ssspmv_csr_f64_range)
+
+def split_tiles(ntiles: int, shards: int) -> list:
+    """Contiguous tile ranges [t0, t1) of nearly equal length, one per shard."""
+    return [(ntiles * g // shards, ntiles * (g + 1) // shards) for g in range(shards)]
+
+
+def spmv_f64_shard(A: DeviceCSR, x: torch.Tensor, y: torch.Tensor, t0: int, t1: int, opts=None,
+                   stream=None) -> np.ndarray:
+    """This shard's rows of y = A x (tiles [t0, t1)) written into y, and its
+    seam record as six floats (row0, row1, status, 0, partial0, partial1)."""
+    r_first, r_last = _c.ssspmv_range_bounds(A.m, A.nnz, A.row_ptr, t0, t1, opts, stream)
+    nbytes = _c.ssspmv_range_workspace_bytes(A.m, A.nnz, t0, t1, r_first, r_last, opts)
+    if nbytes <= 0:
+        raise _c.SsspmvError(_c.SSSPMV_EINVAL, "ssspmv_range_workspace_bytes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=x.device)
+    seam = torch.zeros(_c.SEAM_BYTES, dtype=torch.uint8, device=x.device)
+    _c.check(_c.ssspmv_csr_f64_range(A.m, A.n, A.nnz, A.row_ptr, A.col, A.val, x, y, t0, t1,
+                                     r_first, r_last, seam, opts=opts, workspace=ws,
+                                     stream=stream), "ssspmv_csr_f64_range")
+    s = _c.seams_from_bytes(seam.cpu().numpy().tobytes())[0]
+    return np.array([s.row[0], s.row[1], s.status, 0, s.val[0], s.val[1]], dtype=np.float64)
+
+
+def merge_seams(records) -> tuple:
+    """Rows cut at shard ends and their final values from the shards' seam
+    records (six floats each, in shard order), through ssspmv_seam_merge."""
+    arr = (_c.ssspmv_seam * len(records))()
+    for d, r in zip(arr, records):
+        d.row[0], d.row[1], d.status = int(r[0]), int(r[1]), int(r[2])
+        d.val[0], d.val[1] = float(r[4]), float(r[5])
+    return _c.ssspmv_seam_merge(arr)

@@ -49,7 +49,8 @@ CLASSES = [
     ("exact W15", dict(W=15, variant=C.VARIANT_EXACT)),
     ("exact W27", dict(W=27, variant=C.VARIANT_EXACT)),
     ("speculative W15, all warps", dict(W=15, variant=C.VARIANT_SPECULATIVE, block_warps=32)),
-    ("speculative W15, 56 KB L1", dict(W=15, variant=C.VARIANT_SPECULATIVE, block_warps=17)),
+    ("speculative W15, 17 warps per block", dict(W=15, variant=C.VARIANT_SPECULATIVE,
+                                                 block_warps=17)),
     ("rows, lanes by mean length", dict(W=0, variant=C.VARIANT_ROWS)),
     ("rows, one lane per row", dict(W=1, variant=C.VARIANT_ROWS)),
 ]

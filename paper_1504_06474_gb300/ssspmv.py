@@ -88,6 +88,11 @@ _SIGS = {
                                        ctypes.c_float, ctypes.c_float, ctypes.c_float, i32, P]),
     "ssspmv_mlp_select": (ctypes.c_int, [P, P, i32, i32, i32, i32, i32, P, P, P]),
     "ssspmv_csr_batched_f32": (ctypes.c_int, [i32, P, i64, OPTS, P, sz, P]),
+    "ssspmv_range_bounds": (ctypes.c_int, [i32, i32, P, OPTS, i64, i64, P, P, P]),
+    "ssspmv_range_workspace_bytes": (sz, [i32, i32, i64, i64, i32, i32, OPTS]),
+    "ssspmv_csr_f64_range": (ctypes.c_int, [i32, i32, i32, P, P, P, P, P, i64, i64, i32, i32, P,
+                                            OPTS, P, sz, P]),
+    "ssspmv_seam_merge": (ctypes.c_int, [i32, P, P, P, P]),
     "ssspmv_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "ssspmv_last_cuda_error": (ctypes.c_int, []),
     "ssspmv_version": (ctypes.c_int, []),
@@ -417,3 +422,55 @@ def ssspmv_last_cuda_error() -> int:
 
 def ssspmv_version() -> int:
     return _lib().ssspmv_version()
+
+
+# --- tile-range shards and their seam records ------------------------------
+
+class ssspmv_seam(ctypes.Structure):
+    _fields_ = [("row", ctypes.c_int32 * 2), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("val", ctypes.c_double * 2)]
+
+
+SEAM_BYTES = ctypes.sizeof(ssspmv_seam)
+
+
+def ssspmv_range_bounds(m, nnz, row_ptr, t0, t1, opts=None, stream=None):
+    """(r_first, r_last) of the tiles [t0, t1); synchronises the stream."""
+    a, b = i32(), i32()
+    check(_lib().ssspmv_range_bounds(m, nnz, _ptr(row_ptr), _opts(opts), t0, t1,
+                                     ctypes.byref(a), ctypes.byref(b), _stream(stream)),
+          "ssspmv_range_bounds")
+    return a.value, b.value
+
+
+def ssspmv_range_workspace_bytes(m, nnz, t0, t1, r_first, r_last, opts=None) -> int:
+    return int(_lib().ssspmv_range_workspace_bytes(m, nnz, t0, t1, r_first, r_last,
+                                                   _opts(opts)))
+
+
+def ssspmv_csr_f64_range(m, n, nnz, row_ptr, col_idx, val, x, y, t0, t1, r_first, r_last, seam,
+                         opts=None, workspace=None, ws_bytes=None, stream=None) -> int:
+    """`seam` is a device buffer of SEAM_BYTES bytes (e.g. a uint8 tensor)."""
+    if ws_bytes is None:
+        ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    return _lib().ssspmv_csr_f64_range(m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(val),
+                                       _ptr(x), _ptr(y), t0, t1, r_first, r_last, _ptr(seam),
+                                       _opts(opts), _ptr(workspace), ws_bytes, _stream(stream))
+
+
+def seams_from_bytes(raw: bytes):
+    """Host seam records from their raw bytes (one or more records)."""
+    n = len(raw) // SEAM_BYTES
+    arr = (ssspmv_seam * n).from_buffer_copy(raw[: n * SEAM_BYTES])
+    return arr
+
+
+def ssspmv_seam_merge(seams):
+    """(rows, vals) of the cut rows from host seam records in shard order."""
+    n = len(seams)
+    arr = (ssspmv_seam * n)(*seams) if not isinstance(seams, ctypes.Array) else seams
+    rows = (ctypes.c_int32 * (2 * max(n, 1)))()
+    vals = (ctypes.c_double * (2 * max(n, 1)))()
+    cnt = i32()
+    check(_lib().ssspmv_seam_merge(n, arr, rows, vals, ctypes.byref(cnt)), "ssspmv_seam_merge")
+    return list(rows[: cnt.value]), list(vals[: cnt.value])

@@ -372,3 +372,45 @@ def test_two_stages_random_structures_within_tolerance():
             y = oracle.checking_stage(A.row_ptr, T, W, S, st)
             assert np.all(np.abs(y - yref) <= 1e-13 * s), (i, T, W, S)
             assert np.all(y[s == 0] == 0.0)
+
+
+# ---------------------------------------------------------------------------
+# the row loop restricted to a range of nonzeros (one shard of a split product)
+
+def test_range_sums_on_the_6x6_example_by_hand():
+    """Entries [4, 9) of the Sec. 2.1 example are e, f (row 1), g, h (row 2)
+    and i (row 4): with x = (1..6) the partial rows are 2e+3f, 3g+5h, 5i."""
+    g = _load("paper_example_6x6.json")
+    sub = {s: float(3 + 2 * i) for i, s in enumerate(g["val_symbols"])}
+    val = np.array([sub[s] for s in g["val_symbols"]])
+    y = oracle.spmv_range(g["row_ptr"], g["col_idx"], val, np.array(g["x"], dtype=float), 4, 9)
+    want = [0.0, 2 * sub["e"] + 3 * sub["f"], 3 * sub["g"] + 5 * sub["h"], 0.0, 5 * sub["i"], 0.0]
+    assert y.tolist() == want
+    # an empty range contributes nothing; the whole range is the plain product
+    assert not oracle.spmv_range(g["row_ptr"], g["col_idx"], val, np.array(g["x"], float), 7,
+                                 7).any()
+    full = oracle.spmv_range(g["row_ptr"], g["col_idx"], val, np.array(g["x"], float), 0, 12)
+    assert full.tolist() == [sum(c * sub[s] for s, c in co.items()) for co in g["y_coefficients"]]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_range_sums_add_up_to_the_product(seed):
+    """Over any partition of [0, nnz) into ranges (cuts inside rows, at row
+    starts, empty ranges) the range sums add up to the row loop's y exactly
+    (small integers: every sum is exact in any order)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lens = rng.integers(0, 60, size=400)
+    lens[rng.integers(0, 400, size=3)] = 3000       # rows over several cuts
+    rp = np.zeros(401, np.int32)
+    np.cumsum(lens, out=rp[1:])
+    nnz = int(rp[-1])
+    col = rng.integers(0, 90, size=nnz).astype(np.int32)
+    val = rng.integers(-7, 8, size=nnz).astype(float)
+    x = rng.integers(-7, 8, size=90).astype(float)
+    cuts = np.unique(np.concatenate([[0, nnz], rng.integers(0, nnz + 1, size=9),
+                                     rp[rng.integers(0, 401, size=3)]]))
+    cuts = np.concatenate([cuts[:2], cuts[1:]])                  # one empty range too
+    total = np.zeros(400)
+    for B, E in zip(cuts[:-1], cuts[1:]):
+        total += oracle.spmv_range(rp, col, val, x, int(B), int(E))
+    assert np.array_equal(total, oracle.spmv(rp, col, val, x))
