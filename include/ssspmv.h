@@ -304,14 +304,14 @@ int ssspmv_mlp_select(const float *params, const float *X, int32_t B, int32_t F,
  * SSSPMV_NOALLOC_SCRATCH_BYTES owned by the library, held by every GPU that
  * loads the library until the process exits.  Problems whose
  * ssspmv_workspace_bytes(m, nnz, 8, opts) exceeds it are rejected with
- * SSSPMV_ETOOLARGE before anything runs (8 MiB covers about 599,000 tiles
- * with the automatic bunch count -- 8 bytes of tile data per tile plus 24
- * bytes of synchronizer record per bunch of 4 -- i.e. nnz up to 287,569,920
+ * SSSPMV_ETOOLARGE before anything runs (8 MiB covers about 466,000 tiles
+ * with the automatic bunch count -- 12 bytes of tile data per tile plus 24
+ * bytes of synchronizer record per bunch of 4 -- i.e. nnz up to 223,671,840
  * at W = 15); options the other calls reject are rejected with the same
  * code.  All calls on a device share the array and it keeps the last call's
  * contents: each call clears its 16-byte header (error word, bunch ticket,
- * schedule flag) with cudaMemsetAsync on `stream`, and the kernels write
- * every other entry before reading it.  Calls that overlap on the GPU race
+ * dirty-tile count, schedule flag) with cudaMemsetAsync on `stream`, and the
+ * kernels write every other entry before reading it.  Calls that overlap on the GPU race
  * on the array -- order them on one stream.  The first call on a device
  * looks up the array's address (cudaGetSymbolAddress) with that device
  * current and caches it; make it before any stream capture begins.

@@ -61,7 +61,8 @@ __device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t *warp
 // One block.  Checks every descriptor (an invalid one is skipped as an empty
 // matrix and flagged), numbers the tiles, bunches and rows of the batch, and
 // writes the records and totals {tiles, bunches} (totals 0 when the batch
-// exceeds the workspace's capacity).  Clears the error word and the ticket.
+// exceeds the workspace's capacity).  Clears the error word, the ticket and the
+// dirty-tile count.
 template <int W>
 __global__ void __launch_bounds__(kPrepThreads)
     batch_prep_kernel(const DescView *__restrict__ desc, int32_t count, int32_t S,
@@ -73,6 +74,7 @@ __global__ void __launch_bounds__(kPrepThreads)
     if (threadIdx.x == 0) {
         err[0] = 0u;
         err[1] = 0u;
+        err[kBatchWordDirty] = 0u;
     }
     __syncthreads();
     const int32_t per = (count + kPrepThreads - 1) / kPrepThreads;
@@ -223,6 +225,8 @@ int run_batched_shape(int32_t count, const void *desc, const BatchLayout &l, uns
         a.tail_flag = reinterpret_cast<int32_t *>(ws + l.off_tflag);
         a.err = err;
         a.ticket = err + 1;
+        a.dirty_count = err + kBatchWordDirty;
+        a.dirty_list = reinterpret_cast<int32_t *>(ws + l.off_dirty);
         a.dbg_desc = nullptr;
         a.m = 0;
         a.nnz = 0;
@@ -271,10 +275,9 @@ int run_batched_shape(int32_t count, const void *desc, const BatchLayout &l, uns
         a.bunch_mat = bmat;
         a.totals = totals;
         a.count = count;
-        int64_t tblk = (l.cap_tiles + kCalibWarps - 1) / kCalibWarps;
-        const int64_t tcap = (int64_t)sms * 16;
-        a.nblk_tiles = (int32_t)(tblk < tcap ? (tblk > 0 ? tblk : 1) : tcap);
-        a.span = calib_span(l.cap_tiles, a.nblk_tiles);
+        a.dirty_count = err + kBatchWordDirty;
+        a.dirty_list = reinterpret_cast<const int32_t *>(ws + l.off_dirty);
+        a.nblk_tiles = calib_tile_blocks(l.cap_tiles);
         a.nblk_sync = (int32_t)((l.cap_bunches + 32 * kCalibWarps - 1) / (32 * kCalibWarps));
         a.nblk_zero = count < 4 * sms ? (count > 0 ? count : 1) : 4 * sms;
         const unsigned grid = (unsigned)(a.nblk_tiles + a.nblk_sync + a.nblk_zero);

@@ -59,7 +59,7 @@ template <class P, int W>
 int segsum_resident_warps(int bw)
 {
     using SM = WarpSmem<P, W>;
-    constexpr BlockShape BS = pick_block_shape(SM::BYTES, P::kMaxWarps);
+    constexpr BlockShape BS = pick_block_shape(SM::BYTES, P::max_warps(W));
     constexpr int B = BS.B;
     static int cache[64][33] = {{0}};
     int dev = 0;
@@ -93,7 +93,7 @@ template <class P, int W>
 int segsum_block_warps(const Call &c)
 {
     using SM = WarpSmem<P, W>;
-    constexpr BlockShape BS = pick_block_shape(SM::BYTES, P::kMaxWarps);
+    constexpr BlockShape BS = pick_block_shape(SM::BYTES, P::max_warps(W));
     constexpr int B = BS.B;
     if (c.block_warps >= 1) return c.block_warps < B ? c.block_warps : B;
     if ((int64_t)c.nnz >= 20 * (int64_t)c.m) return B;
@@ -103,13 +103,16 @@ int segsum_block_warps(const Call &c)
     return l1w < B ? l1w : B;
 }
 
-// tiles per warp window of kernel (c)'s tile role: the tiles spread evenly
-// over its warps, read in one round of loads (at most 32 per window)
-inline int32_t calib_span(int64_t ntiles, int32_t nblk_tiles)
+// blocks of kernel (c)'s tile role: a warp per tile for small matrices (any
+// of them may be dirty), at most one wave (six blocks of eight warps per SM
+// next to the synchronizer and zeroing roles); its warps stride over the
+// dirty tiles kernel (b) listed
+inline int32_t calib_tile_blocks(int64_t ntiles)
 {
-    const int64_t nw = (int64_t)(nblk_tiles > 0 ? nblk_tiles : 1) * kCalibWarps;
-    int64_t s = (ntiles + nw - 1) / nw;
-    return (int32_t)(s < 1 ? 1 : (s > 32 ? 32 : s));
+    int64_t b = (ntiles + kCalibWarps - 1) / kCalibWarps;
+    const int64_t cap = 6LL * device_sm_count();
+    if (b > cap) b = cap;
+    return (int32_t)(b < 1 ? 1 : b);
 }
 
 // kernel (c)'s shared memory: one buffer of L+1 partials per warp (the
@@ -146,7 +149,7 @@ template <class P, int W>
 int run_shape(const Call &c)
 {
     using SM = WarpSmem<P, W>;
-    constexpr BlockShape BS = pick_block_shape(SM::BYTES, P::kMaxWarps);
+    constexpr BlockShape BS = pick_block_shape(SM::BYTES, P::max_warps(W));
     constexpr int B = BS.B;
     const Layout &l = c.lay;
     unsigned char *ws = c.ws;
@@ -162,9 +165,10 @@ int run_shape(const Call &c)
     if (c.ev && (e = cudaEventRecord(c.ev[0], c.stream)) != cudaSuccess)
         return record_cuda_error(e);
     if (c.skip_partition) {
-        // the partition is the plan's; only the error word and the bunch
-        // ticket (cleared by kernel (a) otherwise) start again from zero
-        if ((e = cudaMemsetAsync(err, 0, 2 * sizeof(uint32_t), c.stream)) != cudaSuccess)
+        // the partition is the plan's; the error word, the bunch ticket and
+        // the dirty-tile count (cleared by kernel (a) otherwise) start again
+        // from zero, the plan's schedule flag stays
+        if ((e = cudaMemsetAsync(err, 0, 3 * sizeof(uint32_t), c.stream)) != cudaSuccess)
             return record_cuda_error(e);
     } else {
         launch_partition(c.row_ptr, c.m, c.nnz, l.L, l.ntiles, toff, err, c.stream,
@@ -186,8 +190,10 @@ int run_shape(const Call &c)
         a.tail_val = tval;
         a.tail_flag = tflag;
         a.err = err;
-        a.ticket = err + 1;
-        a.spread = err + 2;
+        a.ticket = err + kWordTicket;
+        a.spread = err + kWordSpread;
+        a.dirty_count = err + kWordDirty;
+        a.dirty_list = reinterpret_cast<int32_t *>(ws + l.off_dirty_list);
         a.dbg_desc = c.dbg_desc;
         a.m = c.m;
         a.nnz = c.nnz;
@@ -240,18 +246,16 @@ int run_shape(const Call &c)
         a.L = l.L;
         a.ntiles = l.ntiles;
         a.nbunches = l.nbunches;
-        // warps of the tile role stride over the tiles (at most 16 per SM's worth)
-        int64_t tblk = (l.ntiles + kCalibWarps - 1) / kCalibWarps;
-        const int64_t tcap = (int64_t)device_sm_count() * 16;
-        a.nblk_tiles = (int32_t)(tblk < tcap ? tblk : tcap);
-        a.span = calib_span(l.ntiles, a.nblk_tiles);
+        a.dirty_count = err + kWordDirty;
+        a.dirty_list = reinterpret_cast<const int32_t *>(ws + l.off_dirty_list);
+        a.nblk_tiles = calib_tile_blocks(l.ntiles);
         a.alpha = c.alpha;
         a.beta = c.beta;
         a.axpby = c.axpby;
         a.nblk_sync = (int32_t)((l.nbunches + 32 * kCalibWarps - 1) / (32 * kCalibWarps));
         a.nblk_zero = kZeroBlocks;
         // the flag of kernel (a) is the plan's when the partition is reused
-        a.spread_reset = c.skip_partition ? nullptr : err + 2;
+        a.spread_reset = c.skip_partition ? nullptr : err + kWordSpread;
         const unsigned grid = (unsigned)(a.nblk_tiles + a.nblk_sync + a.nblk_zero);
         const size_t smem = calib_smem_bytes<P>(l.L);
         if ((e = calib_smem_attr<P, false>(smem)) != cudaSuccess) return record_cuda_error(e);

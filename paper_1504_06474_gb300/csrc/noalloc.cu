@@ -13,9 +13,10 @@
 // Every GPU that loads this library holds it until the process exits.  All
 // calls on a device share it and it keeps the last call's contents.  Each
 // call clears the array's 16-byte header on its stream first (the device
-// error word, the bunch ticket and kernel (b)'s schedule flag, which a call
-// that stopped between kernels (b) and (c) could otherwise leave set); the
-// kernels write every other entry before they read it.  Calls whose kernels
+// error word, the bunch ticket, the dirty-tile count and kernel (b)'s
+// schedule flag, which a call that stopped between kernels (b) and (c) could
+// otherwise leave set); the kernels write every other entry before they read
+// it.  Calls whose kernels
 // overlap on the GPU (different streams, no ordering between them) race on
 // the shared array and corrupt each other's results: order them on one
 // stream or through events.

@@ -21,9 +21,10 @@ __global__ void __launch_bounds__(kPartitionThreads)
     grid_dep_trigger();  // kernel (b) may launch its blocks as these finish
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) {
-        err[0] = 0u;  // device error word
-        err[1] = 0u;  // bunch ticket of kernel (b)
-        err[2] = 1u;  // tiles span 64 rows on average: spread the schedule
+        err[kWordErr] = 0u;
+        err[kWordTicket] = 0u;
+        err[kWordDirty] = 0u;
+        err[kWordSpread] = 1u;  // tiles span 64 rows on average: spread the schedule
     }
     if (t > ntiles) return;
     const int64_t bl = t * (int64_t)L;
@@ -53,8 +54,9 @@ __global__ void __launch_bounds__(kPartitionThreads)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i0 == 0) {
-        err[0] = 0u;  // device error word
-        err[1] = 0u;  // bunch ticket of kernel (b)
+        err[kWordErr] = 0u;
+        err[kWordTicket] = 0u;
+        err[kWordDirty] = 0u;
         tile_offset[ntiles] = m;  // b = nnz: every row pointer is <= nnz
     }
     // every lane of a warp runs the same iterations (the ballots need them)
@@ -73,11 +75,11 @@ __global__ void __launch_bounds__(kPartitionThreads)
             // written by the whole warp
             const int64_t r = r0 + u * stride;
             // 32 consecutive empty rows (sampled: first chunk of four): flag
-            // for kernel (b)'s schedule (err[2] is cleared by kernel (c) of
+            // for kernel (b)'s schedule (the flag is cleared by kernel (c) of
             // the call before)
             if (u == 0 &&
                 __ballot_sync(0xffffffffu, lo[u] != hi[u] || r >= m) == 0u && (threadIdx.x & 31) == 0)
-                err[2] = 1u;
+                err[kWordSpread] = 1u;
             const int64_t tlo = ((uint32_t)lo[u] + (uint32_t)(L - 1)) / (uint32_t)L;
             const int64_t thi = ((uint32_t)hi[u] + (uint32_t)(L - 1)) / (uint32_t)L;
             const bool longrow = thi - tlo > 8;

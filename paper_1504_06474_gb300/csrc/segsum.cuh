@@ -30,7 +30,8 @@ namespace ssspmv {
 // precision traits
 
 struct F64 {
-    static constexpr int kMaxWarps = 32;  // shared memory decides
+    // most warps per SM that the registers allow at tile width W
+    static constexpr int max_warps(int) { return 32; }  // shared memory decides
     static constexpr int kShortRowWarps = 14;  // short rows: keep L1 for the gathers (measured)
     using val_t = double;
     using x_t = double;
@@ -83,9 +84,13 @@ __device__ __forceinline__ CompF32 comp_fma(float v, float x, CompF32 a)
 
 template <class V>
 struct CompF32Traits {
-    // FP32 values: 24 warps (85 registers per thread, no spills at W = 15);
-    // BF16 values need more registers for the widening: 20 (96)
-    static constexpr int kMaxWarps = std::is_same<V, float>::value ? 24 : 20;
+    // FP32 values: 24 warps (80 registers per thread, no spills at W = 15);
+    // BF16 values: 24 at W = 15 (80 registers, no spills), 20 for longer
+    // tiles, whose widened values need 96 registers
+    static constexpr int max_warps(int W)
+    {
+        return (std::is_same<V, float>::value || W <= 15) ? 24 : 20;
+    }
     static constexpr int kBatchMaxWarps = 20;  // the batched kernel needs more registers
     static constexpr int kShortRowWarps = 16;  // short rows: keep L1 for the gathers (measured)
     using val_t = V;
@@ -212,6 +217,10 @@ struct SegsumArgs {
     int32_t *tail_flag;
     uint32_t *err;
     uint32_t *ticket;    // bunch ticket counter, zero at launch
+    // dirty tiles left speculative are appended here for kernel (c) (the
+    // paper's speculator and dirty counter); the count is zero at launch
+    uint32_t *dirty_count = nullptr;
+    int32_t *dirty_list = nullptr;
     // nullable: nonzero when kernel (a) saw a run of 32 empty rows (tiles
     // over thousands of rows may follow): a smaller static share then
     const uint32_t *spread = nullptr;
@@ -778,9 +787,15 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
                     emit(nseg - 1, C, openpos);
                 }
             }
-            if (lane == 0)
+            if (lane == 0) {
                 a.tile_info[t] = (uint32_t)nseg | (dirty ? kInfoDirty : 0u) |
                                  (resolve ? kInfoResolved : 0u);
+                if (dirty && !resolve) {  // kernel (c) re-arranges it
+                    const uint32_t pos = atomicAdd(a.dirty_count, 1u);
+                    if (pos < (uint32_t)ntiles) a.dirty_list[pos] = t;
+                    else atomicOr(a.err, SSSPMV_DEV_CALIB);
+                }
+            }
             __syncwarp();
             carry = *slot_carry;
             ++q_con;
@@ -833,10 +848,11 @@ struct CalibArgs {
     int32_t L;
     int64_t ntiles;
     int64_t nbunches;
+    const uint32_t *dirty_count;  // written by kernel (b)
+    const int32_t *dirty_list;
     int32_t nblk_tiles;
     int32_t nblk_sync;
     int32_t nblk_zero;
-    int32_t span;  // tiles per warp window of the tile role (1..32)
     uint32_t *spread_reset = nullptr;  // kernel (b)'s schedule flag, cleared here
     double alpha = 1.0, beta = 0.0;  // y = alpha A x + beta y (see SegsumArgs)
     int32_t axpby = 0;
@@ -873,16 +889,22 @@ __device__ __forceinline__ void repair_dirty_tile(const int32_t *__restrict__ ro
         if (lane == 0) atomicOr(err, SSSPMV_DEV_CALIB);
         return;
     }
-    for (int32_t q = 1 + lane; q <= K; q += 32) part[q] = y[start + q];
-    __syncwarp();
     auto rp = [&](int32_t r) { return __ldg(row_ptr + (r < m ? r : m)); };
     constexpr int CH = 8;
+    // the first chunk of row pointers is loaded together with the partials
+    int32_t pr[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) pr[u] = rp(start + 1 + 32 * u + lane);
+    int32_t tail = (lane == 31) ? rp(start + 1 + 32 * CH) : 0;
+    for (int32_t q = 1 + lane; q <= K; q += 32) part[q] = y[start + q];
+    __syncwarp();
     int32_t before = 0;  // non-empty rows in (start, r) so far
     for (int32_t rb = start + 1; rb < stop; rb += 32 * CH) {
-        int32_t pr[CH];
+        if (rb != start + 1) {
 #pragma unroll
-        for (int u = 0; u < CH; ++u) pr[u] = rp(rb + 32 * u + lane);
-        const int32_t tail = (lane == 31) ? rp(rb + 32 * CH) : 0;
+            for (int u = 0; u < CH; ++u) pr[u] = rp(rb + 32 * u + lane);
+            tail = (lane == 31) ? rp(rb + 32 * CH) : 0;
+        }
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
             const int32_t r = rb + 32 * u + lane;
@@ -1018,22 +1040,22 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
     int blk = blockIdx.x;
 
     if (blk < a.nblk_tiles) {
-        // ---- re-arrangement of dirty tiles (Sec. 3.2, checking prediction):
-        // the warps of this role stride over the tiles
-        // (warp w takes tiles w, w + nw, w + 2 nw, ...: dirty tiles cluster,
-        // so striding spreads them over the warps; `span` of them are read in
-        // one round of loads, then the dirty ones are repaired in turn)
-        // Consecutive tiles go to consecutive blocks (tile t to the warp with
-        // block-major index t mod nw), so tiles over many rows, which
-        // cluster, spread over the blocks: each warp defers those to its
-        // block, which re-arranges them with all its warps at the end.
+        // ---- re-arrangement of dirty tiles (Sec. 3.2, checking prediction).
+        // Kernel (b) appended every dirty tile it left speculative to a list
+        // (the paper's speculator, in any order); the warps of this role
+        // stride over it, consecutive entries going to consecutive blocks,
+        // and read up to 32 of their entries and tile flags in one round of
+        // loads.  A dirty tile over more than kLongRepairRows rows is
+        // deferred to its block, which re-arranges it with all its warps at
+        // the end.
         __shared__ int64_t s_long[kLongListCap];
         __shared__ uint32_t s_linfo[kLongListCap];
         __shared__ int32_t s_nlong, s_cnt[kCalibWarps];
         if (threadIdx.x == 0) s_nlong = 0;
         __syncthreads();
         const int64_t nw = (int64_t)a.nblk_tiles * kCalibWarps;
-        const int64_t span = a.span;
+        int64_t count = (int64_t)*(volatile const uint32_t *)a.dirty_count;
+        if (count > ntiles) count = ntiles;  // kernel (b) appends each tile at most once
         // the matrix data of global tile t (in a batch: of its matrix)
         struct Tile {
             const int32_t *row_ptr;
@@ -1056,16 +1078,33 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
                             __ldg(a.tile_offset + t + 1), t};
             }
         };
-        for (int64_t t0 = (int64_t)warp * a.nblk_tiles + blk; t0 < ntiles; t0 += nw * span) {
-            const int64_t tl = t0 + (int64_t)lane * nw;
-            const uint32_t il = (lane < span && tl < ntiles) ? __ldg(a.tile_info + tl) : 0u;
-            unsigned todo = __ballot_sync(FULL, (il & kInfoDirty) && !(il & kInfoResolved));
+        for (int64_t i0 = (int64_t)warp * a.nblk_tiles + blk; i0 < count; i0 += nw * 32) {
+            const int64_t il = i0 + (int64_t)lane * nw;
+            const int64_t tl = il < count ? (int64_t)__ldg(a.dirty_list + il) : -1;
+            const bool okt = tl >= 0 && tl < ntiles;
+            const uint32_t infl = okt ? __ldg(a.tile_info + tl) : 0u;
+            // (single matrix) the window's tile offsets in the same round
+            int32_t st_l = 0, sp_l = 0;
+            if (!BATCHED && okt) {
+                st_l = __ldg(a.tile_offset + tl);
+                sp_l = __ldg(a.tile_offset + tl + 1);
+            }
+            // an entry must name a dirty tile that kernel (b) did not resolve
+            const bool good = okt && (infl & kInfoDirty) && !(infl & kInfoResolved);
+            if (il < count && !good) atomicOr(a.err, SSSPMV_DEV_CALIB);
+            unsigned todo = __ballot_sync(FULL, good);
             while (todo) {
                 const int src = __ffs(todo) - 1;
                 todo &= todo - 1;
-                const int64_t t = t0 + (int64_t)src * nw;
-                const uint32_t info = __shfl_sync(FULL, il, src);
-                const Tile T = tile_of(t);
+                const int64_t t = __shfl_sync(FULL, tl, src);
+                const uint32_t info = __shfl_sync(FULL, infl, src);
+                Tile T;
+                if constexpr (BATCHED) {
+                    T = tile_of(t);
+                } else {
+                    T = Tile{a.row_ptr, y, a.m, a.nnz, __shfl_sync(FULL, st_l, src),
+                             __shfl_sync(FULL, sp_l, src), t};
+                }
                 if (T.stop - T.start > kLongRepairRows) {
                     int slot = 0;
                     if (lane == 0) slot = atomicAdd(&s_nlong, 1);
@@ -1159,12 +1198,25 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
             const int32_t rr = (int32_t)(kk & 0xffffffff);
             const double csum = __shfl_sync(FULL, C, 31);
             const int64_t wl = base + __shfl_sync(FULL, first, 31);
+            // eight windows of 32 bunches per round trip of loads (a row of
+            // 10^6 entries spans hundreds of bunches); each lane still adds
+            // its bunches in increasing order, so the sum does not change
+            constexpr int U = 8;
             double acc = 0.0;
-            for (int64_t b2 = base + 32;; b2 += 32) {
-                const int64_t ww = b2 + lane;
-                const bool in = ww < nbunches && key_of(ww) == kk;
-                if (in) acc += sv[ww];
-                if (__popc(__ballot_sync(FULL, in)) < 32) break;
+            for (int64_t b2 = base + 32;; b2 += 32 * U) {
+                bool in[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t ww = b2 + 32 * u + lane;
+                    in[u] = ww < nbunches && key_of(ww) == kk;
+                }
+                bool full = true;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (in[u]) acc += sv[b2 + 32 * u + lane];
+                    full = full && __all_sync(FULL, in[u]);
+                }
+                if (!full) break;
             }
 #pragma unroll
             for (int d = 16; d >= 1; d >>= 1) acc += __shfl_xor_sync(FULL, acc, d);

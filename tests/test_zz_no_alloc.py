@@ -35,9 +35,10 @@ def test_rejects_problems_beyond_the_fixed_scratch(lib):
 
 
 # the largest nnz whose workspace fits the fixed scratch with the default
-# options (W = 15, 4 tiles per bunch): 8 bytes per tile plus a 24-byte
-# synchronizer record per bunch, each section 256-byte aligned
-NOALLOC_MAX_NNZ = 287_569_920
+# options (W = 15, 4 tiles per bunch): 12 bytes per tile (offset, info, dirty
+# list entry) plus a 24-byte synchronizer record per bunch, each section
+# 256-byte aligned
+NOALLOC_MAX_NNZ = 223_671_840
 
 
 def test_capacity_boundary(lib):
