@@ -32,6 +32,9 @@ namespace ssspmv {
 struct F64 {
     // most warps per SM that the registers allow at tile width W
     static constexpr int max_warps(int) { return 32; }  // shared memory decides
+    // scan the rows of a tile over many rows before its gathers (measured:
+    // R-MAT scale 22 kernel (b) 362 -> 350 us; the FP32 forms lose 2-3%)
+    static constexpr bool kEarlyLongScan = true;
     static constexpr int kShortRowWarps = 14;  // short rows: keep L1 for the gathers (measured)
     using val_t = double;
     using x_t = double;
@@ -92,6 +95,7 @@ struct CompF32Traits {
         return (std::is_same<V, float>::value || W <= 15) ? 24 : 20;
     }
     static constexpr int kBatchMaxWarps = 20;  // the batched kernel needs more registers
+    static constexpr bool kEarlyLongScan = false;  // see F64
     static constexpr int kShortRowWarps = 16;  // short rows: keep L1 for the gathers (measured)
     using val_t = V;
     using x_t = float;
@@ -259,20 +263,21 @@ constexpr uint32_t kInfoSegMask = 0x3fffffffu;
 
 // ---------------------------------------------------------------------------
 // descriptor scan of rows [rb0, stop] for tiles over many (mostly empty) rows,
-// four chunks of 32 rows per round trip.  A run of empty rows shares one row
+// CH chunks of 32 rows per round trip.  A run of empty rows shares one row
 // pointer: only its last row (the non-empty row, or `stop`) sets the bit, so
 // the atomics do not pile up on one word.  Kept out of line: the call is rare
-// and the loop then keeps its loads in flight with registers of its own
-// instead of competing with the tile's gathered x.  Returns bit 0: an empty
-// row in [rb0, stop); bit 1: row `stop` starts inside the tile.  With exact
-// stores (xs) it also writes the position-to-row map and zeroes the empty rows.
-template <class Y>
+// and the loop then keeps its loads in flight with registers of its own.
+// Called with CH = 16 before a tile's gathers are issued (no gathered x held
+// in registers), with CH = 4 after them (more would spill the FP64 kernel's
+// registers).  Returns bit 0: an empty row in [rb0, stop); bit 1: row `stop`
+// starts inside the tile.  With exact stores (xs) it also writes the
+// position-to-row map and zeroes the empty rows.
+template <class Y, int CH>
 __device__ __noinline__ uint32_t scan_rows_long(const int32_t *__restrict__ row_ptr, int32_t m,
                                                 int32_t rb0, int32_t stop, int32_t b, int32_t len,
                                                 uint32_t *desc, int32_t *rowmap, Y *y,
                                                 double alpha, double beta, int32_t axpby, bool xs)
 {
-    constexpr int CH = 4;  // more would spill the FP64 kernel's registers
     const int lane = threadIdx.x & 31;
     const int32_t e = b + len;
     uint32_t flags = 0;
@@ -606,6 +611,22 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
                 __syncwarp();
             }
 
+            // ---- a tile over many rows with speculative FP64 stores: its rows
+            // past the first 64 (usually thousands of mostly empty rows at the
+            // sparse end of a power-law matrix) are scanned before the gathers
+            // are issued, when no gathered x is held in registers, so the scan
+            // keeps 16 chunks of row pointers in flight.  (Exact stores scan
+            // after the gathers: their row map goes into the column region
+            // the gathers read.)
+            uint32_t long_flags = 0;
+            const bool long_first = P::kEarlyLongScan && !EXACT && start + 64 <= stop;
+            if (long_first) {
+                if (lane <= W) desc[lane] = 0u;
+                __syncwarp();
+                long_flags = scan_rows_long<Y, 16>(row_ptr, mrows, start + 64, stop, b, len, desc,
+                                                   nullptr, y, a.alpha, a.beta, a.axpby, false);
+            }
+
             // ---- gathers of x for the lane's W entries (Alg. 1 products),
             // issued before the descriptor work so their latency overlaps it
             X xv[W];
@@ -624,9 +645,9 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
             // once the gathers above are issued) and empty rows are zeroed.
             int32_t *rowmap = reinterpret_cast<int32_t *>(st + SM::VAL_REGION);
             constexpr bool xs = EXACT;
-            if (lane <= W) desc[lane] = 0u;
+            if (!long_first && lane <= W) desc[lane] = 0u;
             __syncwarp();
-            bool dirty = false, cont = false, raw0 = false;
+            bool dirty = (long_flags & 1u) != 0, cont = (long_flags & 2u) != 0, raw0 = false;
             auto scan_row = [&](int32_t r, int32_t pr, int32_t nx) {
                 if (r > stop) return;
                 const int32_t k = pr - b;
@@ -656,10 +677,10 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
                 int32_t nx = __shfl_down_sync(FULL, pr_chunk2, 1);
                 if (lane == 31 && start + 63 < stop) nx = rp_at(start + 64);
                 scan_row(start + 32 + lane, pr_chunk2, nx);
-                if (start + 64 <= stop) {  // long row ranges
-                    const uint32_t f = scan_rows_long<Y>(row_ptr, mrows, start + 64, stop, b, len,
-                                                         desc, rowmap, y, a.alpha, a.beta, a.axpby,
-                                                         xs);
+                if (!long_first && start + 64 <= stop) {  // long row ranges, exact stores
+                    const uint32_t f = scan_rows_long<Y, 4>(row_ptr, mrows, start + 64, stop, b,
+                                                            len, desc, rowmap, y, a.alpha, a.beta,
+                                                            a.axpby, xs);
                     dirty |= (f & 1u) != 0;
                     cont |= (f & 2u) != 0;
                 }
