@@ -217,7 +217,7 @@ static int cached_workspace(size_t need, void *stream, void **ptr, size_t *bytes
     slot->bytes = want - (a - (uintptr_t)base);
     // the error words at the front start cleared (kernel (b)'s schedule
     // flag is read before the first call's kernel (c) clears it)
-    if ((e = cudaMemsetAsync(slot->ptr, 0, 16, s)) != cudaSuccess) return record_cuda_error(e);
+    if ((e = cudaMemsetAsync(slot->ptr, 0, kHeaderBytes, s)) != cudaSuccess) return record_cuda_error(e);
     *ptr = slot->ptr;
     *bytes = slot->bytes;
     return SSSPMV_OK;
@@ -580,7 +580,7 @@ int ssspmv_plan_create(int32_t m, int32_t n, int32_t nnz, const int32_t *row_ptr
         // kernel (a) alone: the tile offsets (and a cleared error word/ticket;
         // the schedule flag it may set starts cleared)
         unsigned char *w = static_cast<unsigned char *>(p->ws);
-        e = cudaMemsetAsync(w + l.off_err, 0, 16, static_cast<cudaStream_t>(stream));
+        e = cudaMemsetAsync(w + l.off_err, 0, kHeaderBytes, static_cast<cudaStream_t>(stream));
         if (e != cudaSuccess) {
             ssspmv_plan_destroy(p);
             return record_cuda_error(e);

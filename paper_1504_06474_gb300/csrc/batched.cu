@@ -277,12 +277,14 @@ int run_batched_shape(int32_t count, const void *desc, const BatchLayout &l, uns
         a.count = count;
         a.dirty_count = err + kBatchWordDirty;
         a.dirty_list = reinterpret_cast<const int32_t *>(ws + l.off_dirty);
-        a.nblk_tiles = calib_tile_blocks(l.cap_tiles);
-        a.nblk_sync = (int32_t)((l.cap_bunches + 32 * kCalibWarps - 1) / (32 * kCalibWarps));
-        a.nblk_zero = count < 4 * sms ? (count > 0 ? count : 1) : 4 * sms;
-        const unsigned grid = (unsigned)(a.nblk_tiles + a.nblk_sync + a.nblk_zero);
         const size_t smem = calib_smem_bytes<P>(l.L);
         if ((e = calib_smem_attr<P, true>(smem)) != cudaSuccess) return record_cuda_error(e);
+        // a warp per matrix zeroes its leading empty rows
+        int32_t nzero = (count + kCalibWarps - 1) / kCalibWarps;
+        if (nzero > kZeroBlocks) nzero = kZeroBlocks;
+        if (nzero < 1) nzero = 1;
+        calib_grid<P, true>(a, l.cap_tiles, l.cap_bunches, nzero, smem);
+        const unsigned grid = (unsigned)(a.nblk_tiles + a.nblk_sync + a.nblk_zero);
         calibrate_kernel<P, true><<<grid, kCalibWarps * 32, smem, stream>>>(a);
     }
     if (ev && (e = cudaEventRecord(ev[3], stream)) != cudaSuccess) return record_cuda_error(e);

@@ -103,18 +103,6 @@ int segsum_block_warps(const Call &c)
     return l1w < B ? l1w : B;
 }
 
-// blocks of kernel (c)'s tile role: a warp per tile for small matrices (any
-// of them may be dirty), at most one wave (six blocks of eight warps per SM
-// next to the synchronizer and zeroing roles); its warps stride over the
-// dirty tiles kernel (b) listed
-inline int32_t calib_tile_blocks(int64_t ntiles)
-{
-    int64_t b = (ntiles + kCalibWarps - 1) / kCalibWarps;
-    const int64_t cap = 6LL * device_sm_count();
-    if (b > cap) b = cap;
-    return (int32_t)(b < 1 ? 1 : b);
-}
-
 // kernel (c)'s shared memory: one buffer of L+1 partials per warp (the
 // repair of a dirty tile), and the attribute that allows it past 48 KB
 template <class P>
@@ -135,6 +123,51 @@ cudaError_t calib_smem_attr(size_t smem)
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) done[dev] = smem;
     return e;
+}
+
+// resident blocks of kernel (c) per SM with `smem` bytes of shared memory
+// (the occupancy query, once per device and size)
+template <class P, bool BATCHED>
+int calib_blocks_per_sm(size_t smem)
+{
+    static int cached[64] = {0};
+    static size_t cached_smem[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (cached[dev] > 0 && cached_smem[dev] == smem) return cached[dev];
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, calibrate_kernel<P, BATCHED>,
+                                                      kCalibWarps * 32, smem) != cudaSuccess ||
+        n < 1) {
+        (void)cudaGetLastError();
+        n = 1;
+    }
+    cached_smem[dev] = smem;
+    cached[dev] = n;
+    return n;
+}
+
+// kernel (c)'s grid, one wave so that no block waits for another to finish:
+// the synchronizer role (its warps stride over windows of 32 bunches; at
+// most a third of the wave), the zeroing role, and the tile role in what is
+// left (a warp per tile for small matrices; its warps stride over the dirty
+// tiles kernel (b) listed)
+template <class P, bool BATCHED>
+void calib_grid(CalibArgs &a, int64_t ntiles, int64_t nbunches, int32_t nzero, size_t smem)
+{
+    const int64_t wave = (int64_t)calib_blocks_per_sm<P, BATCHED>(smem) * device_sm_count();
+    int64_t sync = (nbunches + 32 * kCalibWarps - 1) / (32 * kCalibWarps);
+    const int64_t sync_cap = wave / 3 > 1 ? wave / 3 : 1;
+    if (sync > sync_cap) sync = sync_cap;
+    if (sync < 1) sync = 1;
+    int64_t tiles = (ntiles + kCalibWarps - 1) / kCalibWarps;
+    int64_t room = wave - sync - nzero;
+    if (tiles > room) tiles = room;
+    if (tiles < 1) tiles = 1;
+    a.nblk_sync = (int32_t)sync;
+    a.nblk_zero = nzero;
+    a.nblk_tiles = (int32_t)tiles;
 }
 
 // S (tiles per bunch) and the bunch count for this call
@@ -248,17 +281,15 @@ int run_shape(const Call &c)
         a.nbunches = l.nbunches;
         a.dirty_count = err + kWordDirty;
         a.dirty_list = reinterpret_cast<const int32_t *>(ws + l.off_dirty_list);
-        a.nblk_tiles = calib_tile_blocks(l.ntiles);
         a.alpha = c.alpha;
         a.beta = c.beta;
         a.axpby = c.axpby;
-        a.nblk_sync = (int32_t)((l.nbunches + 32 * kCalibWarps - 1) / (32 * kCalibWarps));
-        a.nblk_zero = kZeroBlocks;
         // the flag of kernel (a) is the plan's when the partition is reused
         a.spread_reset = c.skip_partition ? nullptr : err + kWordSpread;
-        const unsigned grid = (unsigned)(a.nblk_tiles + a.nblk_sync + a.nblk_zero);
         const size_t smem = calib_smem_bytes<P>(l.L);
         if ((e = calib_smem_attr<P, false>(smem)) != cudaSuccess) return record_cuda_error(e);
+        calib_grid<P, false>(a, l.ntiles, l.nbunches, kZeroBlocks, smem);
+        const unsigned grid = (unsigned)(a.nblk_tiles + a.nblk_sync + a.nblk_zero);
         e = launch_dependent(calibrate_kernel<P, false>, grid, kCalibWarps * 32, smem, c.stream, a);
         if (e != cudaSuccess) return record_cuda_error(e);
     }

@@ -35,6 +35,7 @@ inline int32_t auto_bunch_tiles(int64_t ntiles)
 // (a plan execution, which skips kernel (a), clears words 0..2 and keeps the
 // plan's flag)
 constexpr int kWordErr = 0, kWordTicket = 1, kWordDirty = 2, kWordSpread = 3;
+constexpr size_t kHeaderBytes = 16;
 
 struct Layout {
     int32_t W = 0, L = 0, S = 0;
@@ -49,7 +50,7 @@ inline void carve(Layout &l)
 {
     size_t o = 0;
     l.off_err = o;
-    o = align256(o + 16);
+    o = align256(o + kHeaderBytes);
     l.off_tile_offset = o;
     o = align256(o + sizeof(int32_t) * (size_t)(l.ntiles + 1));
     l.off_tile_info = o;

@@ -33,6 +33,7 @@
 
 #include <mutex>
 
+#include "layout.h"
 #include "ssspmv.h"
 
 namespace ssspmv {
@@ -92,7 +93,7 @@ extern "C" int ssspmv_csr_f64_noalloc(int32_t m, int32_t n, int32_t nnz, const i
         scratch = g_scratch_addr[dev];
     }
     if (m > 0) {
-        e = cudaMemsetAsync(scratch, 0, 16, st);
+        e = cudaMemsetAsync(scratch, 0, ssspmv::kHeaderBytes, st);
         if (e != cudaSuccess) return ssspmv::record_cuda_error(e);
     }
     return ssspmv_csr_f64(m, n, nnz, row_ptr, col_idx, val, x, y, opts, scratch,

@@ -44,15 +44,20 @@ __global__ void __launch_bounds__(kPartitionThreads)
 // row_ptr[r+1]), which is the rightmost row with row_ptr[r] <= b_t; so each
 // non-empty row writes its index to the boundaries it contains.  Reads
 // row_ptr once, coalesced, instead of ~log2(m) dependent probes per boundary.
+// All index arithmetic is 32-bit (m, nnz and the tile count are below 2^31,
+// and r0 + 7 * stride stays below 2^32): the kernel is bound by instruction
+// issue, not by its 4 bytes per row.
 template <int W>
 __global__ void __launch_bounds__(kPartitionThreads)
     partition_scatter_kernel(const int32_t *__restrict__ row_ptr, int32_t m, int32_t nnz,
                              int64_t ntiles, int32_t *__restrict__ tile_offset, uint32_t *err)
 {
-    constexpr int64_t L = 32 * W;  // a compile-time divisor
+    constexpr uint32_t L = 32u * W;  // a compile-time divisor
     grid_dep_trigger();  // kernel (b) may launch its blocks as these finish
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t mu = (uint32_t)m;
     if (i0 == 0) {
         err[kWordErr] = 0u;
         err[kWordTicket] = 0u;
@@ -60,39 +65,39 @@ __global__ void __launch_bounds__(kPartitionThreads)
         tile_offset[ntiles] = m;  // b = nnz: every row pointer is <= nnz
     }
     // every lane of a warp runs the same iterations (the ballots need them)
-    const int64_t warp0 = i0 - (threadIdx.x & 31);
-    for (int64_t r0 = i0; warp0 + (r0 - i0) < m; r0 += 4 * stride) {
-        int32_t lo[4], hi[4];
+    const uint32_t warp0 = i0 - lane;
+    for (uint32_t r0 = i0; warp0 + (r0 - i0) < mu; r0 += 4u * stride) {
+        uint32_t lo[4], hi[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {  // four independent rows in flight
-            const int64_t r = r0 + u * stride;
-            lo[u] = r < m ? __ldg(row_ptr + r) : 0;
-            hi[u] = r < m ? __ldg(row_ptr + r + 1) : 0;
+            const uint32_t r = r0 + (uint32_t)u * stride;
+            const bool in = r < mu;
+            lo[u] = in ? (uint32_t)__ldg(row_ptr + r) : 0u;
+            hi[u] = in ? (uint32_t)__ldg(row_ptr + r + 1) : 0u;
         }
+        // 32 consecutive empty rows (sampled: the first of the four chunks):
+        // flag for kernel (b)'s schedule (cleared by kernel (c) of the call
+        // before)
+        if (__ballot_sync(0xffffffffu, lo[0] != hi[0] || r0 >= mu) == 0u && lane == 0)
+            err[kWordSpread] = 1u;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             // tiles t with lo <= t*L < hi; a row spanning many tiles is
             // written by the whole warp
-            const int64_t r = r0 + u * stride;
-            // 32 consecutive empty rows (sampled: first chunk of four): flag
-            // for kernel (b)'s schedule (the flag is cleared by kernel (c) of
-            // the call before)
-            if (u == 0 &&
-                __ballot_sync(0xffffffffu, lo[u] != hi[u] || r >= m) == 0u && (threadIdx.x & 31) == 0)
-                err[kWordSpread] = 1u;
-            const int64_t tlo = ((uint32_t)lo[u] + (uint32_t)(L - 1)) / (uint32_t)L;
-            const int64_t thi = ((uint32_t)hi[u] + (uint32_t)(L - 1)) / (uint32_t)L;
-            const bool longrow = thi - tlo > 8;
+            const uint32_t r = r0 + (uint32_t)u * stride;
+            const uint32_t tlo = (lo[u] + (L - 1u)) / L;
+            const uint32_t thi = (hi[u] + (L - 1u)) / L;
+            const bool longrow = thi - tlo > 8u;
             if (!longrow)
-                for (int64_t t = tlo; t < thi; ++t) tile_offset[t] = (int32_t)r;
+                for (uint32_t t = tlo; t < thi; ++t) tile_offset[t] = (int32_t)r;
             unsigned lm = __ballot_sync(0xffffffffu, longrow);
             while (lm) {
                 const int src = __ffs(lm) - 1;
                 lm &= lm - 1;
-                const int64_t a = __shfl_sync(0xffffffffu, tlo, src);
-                const int64_t z = __shfl_sync(0xffffffffu, thi, src);
-                const int32_t rr = (int32_t)__shfl_sync(0xffffffffu, r, src);
-                for (int64_t t = a + (threadIdx.x & 31); t < z; t += 32) tile_offset[t] = rr;
+                const uint32_t a = __shfl_sync(0xffffffffu, tlo, src);
+                const uint32_t z = __shfl_sync(0xffffffffu, thi, src);
+                const uint32_t rr = __shfl_sync(0xffffffffu, r, src);
+                for (uint32_t t = a + lane; t < z; t += 32u) tile_offset[t] = (int32_t)rr;
             }
         }
     }

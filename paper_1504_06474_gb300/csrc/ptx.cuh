@@ -109,6 +109,21 @@ __device__ __forceinline__ float ldg_keep(const float *p, uint64_t pol)
     return v;
 }
 
+// element copy global -> shared that does not hold the thread: the data
+// lands in shared memory asynchronously, and cp_async_wait_all() waits for
+// every such copy this thread issued (other threads then need a barrier).
+// dst and src aligned to sizeof(T), which is 4, 8 or 16.
+template <class T>
+__device__ __forceinline__ void cp_async_g2s(T *dst, const T *src)
+{
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8 || sizeof(T) == 16, "cp.async size");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "n"((int)sizeof(T))
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // programmatic dependent launch: a kernel launched with the programmatic
 // stream-serialization attribute may start while the kernel before it on the
 // stream is still running.  grid_dep_wait() returns once that kernel has

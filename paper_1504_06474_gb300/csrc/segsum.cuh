@@ -261,6 +261,11 @@ constexpr uint32_t kInfoDirty = 0x80000000u;
 constexpr uint32_t kInfoResolved = 0x40000000u;
 constexpr uint32_t kInfoSegMask = 0x3fffffffu;
 
+// dirty tiles over more rows than this are re-arranged by a whole block in
+// kernel (c), which keeps up to kLongListCap of them at a time
+constexpr int32_t kLongRepairRows = 1024;
+constexpr int kLongListCap = 512;
+
 // ---------------------------------------------------------------------------
 // descriptor scan of rows [rb0, stop] for tiles over many (mostly empty) rows,
 // CH chunks of 32 rows per round trip.  A run of empty rows shares one row
@@ -849,10 +854,10 @@ __global__ void __launch_bounds__(B * 32, MINB) segsum_kernel(const SegsumArgs a
 }
 
 // ---------------------------------------------------------------------------
-// kernel (c): calibration.  Block roles by blockIdx.x:
-//   [0, nblk_tiles)                 one warp per tile: re-arrange dirty tiles
-//   [nblk_tiles, +nblk_sync)        one warp per bunch: synchronizer sums
-//   [..., +nblk_zero)               grid-stride zeroing of leading empty rows
+// kernel (c): calibration.  Block roles by blockIdx.x (the grid is one wave):
+//   [0, nblk_sync)                  synchronizer sums, a warp per 32 bunches
+//   [nblk_sync, +nblk_zero)         grid-stride zeroing of leading empty rows
+//   [..., +nblk_tiles)              re-arrangement of the listed dirty tiles
 
 struct CalibArgs {
     const int32_t *row_ptr;
@@ -886,12 +891,30 @@ struct CalibArgs {
 
 constexpr int kCalibWarps = 8;
 
+// the partials of dirty tile t (index in its matrix, rows [start, stop]) that
+// belong to rows strictly inside (start, stop): one per non-empty row there,
+// i.e. the tile's segments but the first and, when the tile's last row goes
+// on into the next tile, the last.  rstop = row_ptr[stop] (any value when
+// stop == m).  -1 when the count is impossible (0 <= K <= L).
+__device__ __forceinline__ int32_t inner_partials(int32_t m, int32_t nnz, int32_t L, int64_t t,
+                                                  int32_t stop, int32_t rstop, uint32_t info)
+{
+    const int32_t nseg = (int32_t)(info & kInfoSegMask);
+    const int64_t e = (t + 1) * (int64_t)L < nnz ? (t + 1) * (int64_t)L : nnz;
+    const bool cont = stop < m && (int64_t)rstop < e;
+    const int32_t K = nseg - 1 - (cont ? 1 : 0);
+    return (K < 0 || K > L) ? -1 : K;
+}
+
 // re-arrangement of one dirty tile by a warp (Sec. 3.2, checking
 // prediction): the s-th partial (s >= 1, speculatively at y[start+s]) moves to
 // the s-th non-empty row inside (start, stop), and the empty rows there become
-// 0.  The K partials are first copied to the warp's shared buffer `part`
-// (K <= L), so the rows can then be written in any order: the warp walks them
-// forwards, eight chunks of 32 rows per round trip of row pointers.
+// 0.  The partials are first read into registers (up to 64) or copied to the
+// warp's shared buffer `part` (K <= L), so the rows can then be written in any
+// order: the warp walks them forwards, eight chunks of 32 rows per round trip
+// of row pointers.  The partials are read with the first chunk of row
+// pointers and row_ptr[stop], so a tile over up to 256 rows costs one round
+// trip of loads.
 // t is the tile's index in its matrix, [start, stop] its rows.
 template <class P>
 __device__ __forceinline__ void repair_dirty_tile(const int32_t *__restrict__ row_ptr,
@@ -903,31 +926,50 @@ __device__ __forceinline__ void repair_dirty_tile(const int32_t *__restrict__ ro
     using Y = typename P::y_t;
     const int32_t nseg = (int32_t)(info & kInfoSegMask);
     const int64_t e = (t + 1) * (int64_t)L < nnz ? (t + 1) * (int64_t)L : nnz;
-    const bool cont = stop < m && (int64_t)__ldg(row_ptr + stop) < e;
-    // non-empty rows strictly inside (start, stop): each holds one segment
+    auto rp = [&](int32_t r) { return __ldg(row_ptr + (r < m ? r : m)); };
+    constexpr int CH = 8;
+    const int32_t rstop = rp(stop);
+    // only the chunks that hold rows of (start, stop) or row_ptr[stop]
+    int32_t pr[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+        pr[u] = start + 1 + 32 * u <= stop ? rp(start + 1 + 32 * u + lane) : 0;
+    int32_t tail = (lane == 31 && start + 1 + 32 * CH <= stop) ? rp(start + 1 + 32 * CH) : 0;
+    // K <= nseg - 1 partials (at most L, inside y): up to 64 stay in
+    // registers, partial q at lane (q-1) % 32 of p0 (q <= 32) or p1; more go
+    // to the warp's shared buffer
+    int32_t qmax = nseg - 1 < L ? nseg - 1 : L;
+    if (qmax > m - 1 - start) qmax = m - 1 - start;
+    const bool inreg = qmax <= 64;
+    Y p0 = Y(0), p1 = Y(0);
+    if (inreg) {
+        if (1 + lane <= qmax) p0 = y[start + 1 + lane];
+        if (33 + lane <= qmax) p1 = y[start + 33 + lane];
+    } else {
+        for (int32_t q = 1 + lane; q <= qmax; q += 32) cp_async_g2s(part + q, y + start + q);
+        cp_async_wait_all();
+    }
+    // the tile's last row goes on into the next tile: its segment is not
+    // among the partials; non-empty rows strictly inside (start, stop) each
+    // hold one segment
+    const bool cont = stop < m && (int64_t)rstop < e;
     const int32_t K = nseg - 1 - (cont ? 1 : 0);
     if (K < 0 || K > L) {
         if (lane == 0) atomicOr(err, SSSPMV_DEV_CALIB);
+        __syncwarp();
         return;
     }
-    auto rp = [&](int32_t r) { return __ldg(row_ptr + (r < m ? r : m)); };
-    constexpr int CH = 8;
-    // the first chunk of row pointers is loaded together with the partials
-    int32_t pr[CH];
-#pragma unroll
-    for (int u = 0; u < CH; ++u) pr[u] = rp(start + 1 + 32 * u + lane);
-    int32_t tail = (lane == 31) ? rp(start + 1 + 32 * CH) : 0;
-    for (int32_t q = 1 + lane; q <= K; q += 32) part[q] = y[start + q];
     __syncwarp();
     int32_t before = 0;  // non-empty rows in (start, r) so far
     for (int32_t rb = start + 1; rb < stop; rb += 32 * CH) {
         if (rb != start + 1) {
 #pragma unroll
-            for (int u = 0; u < CH; ++u) pr[u] = rp(rb + 32 * u + lane);
-            tail = (lane == 31) ? rp(rb + 32 * CH) : 0;
+            for (int u = 0; u < CH; ++u) pr[u] = rb + 32 * u <= stop ? rp(rb + 32 * u + lane) : 0;
+            tail = (lane == 31 && rb + 32 * CH <= stop) ? rp(rb + 32 * CH) : 0;
         }
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
+            if (rb + 32 * u >= stop) break;  // no rows of the tile left
             const int32_t r = rb + 32 * u + lane;
             const int32_t lead = __shfl_sync(FULL, pr[u < CH - 1 ? u + 1 : CH - 1], 0);
             int32_t nx = __shfl_down_sync(FULL, pr[u], 1);
@@ -936,10 +978,16 @@ __device__ __forceinline__ void repair_dirty_tile(const int32_t *__restrict__ ro
             const bool ne = valid && nx > pr[u];
             const unsigned mask = __ballot_sync(FULL, ne);
             const int32_t q = before + 1 + __popc(mask & ((1u << lane) - 1u));
+            Y pq = Y(0);
+            if (inreg) {
+                const Y a0 = __shfl_sync(FULL, p0, (q - 1) & 31);
+                const Y a1 = __shfl_sync(FULL, p1, (q - 1) & 31);
+                pq = q <= 32 ? a0 : a1;
+            }
             if (valid) {
                 Y v = Y(0);
                 if (ne) {
-                    if (q <= K) v = part[q];
+                    if (q <= K) v = inreg ? pq : part[q];
                     else atomicOr(err, SSSPMV_DEV_CALIB);
                 }
                 y[r] = v;
@@ -951,47 +999,44 @@ __device__ __forceinline__ void repair_dirty_tile(const int32_t *__restrict__ ro
     __syncwarp();  // the buffer is reused for the warp's next tile
 }
 
-// dirty tiles over more rows than this are re-arranged by a whole block
-constexpr int32_t kLongRepairRows = 1024;
-constexpr int kLongListCap = 64;  // such tiles a block defers (more: by a warp)
 
 // the same re-arrangement by all kCalibWarps warps of a block, for a tile
-// over many rows: each warp takes a contiguous share of (start, stop), counts
-// its non-empty rows (first pass), and after a block barrier moves the
-// partials from its count prefix on (second pass).  Every thread of the block
-// calls it with the same arguments; part holds L+1 values, cnt kCalibWarps.
+// over many rows with K inner partials (inner_partials, checked by the
+// caller): each warp takes a contiguous share of (start, stop) and
+// counts its non-empty rows, keeping their flags as bit masks in `bits`
+// (first pass, the only one that loads row pointers); after a block barrier
+// it moves the partials from its count prefix on (second pass: stores
+// only).  A tile over more than 32 * bits_words rows walks the row pointers
+// again in the second pass.  Every thread of the block calls it with the
+// same arguments; part holds L+1 values, cnt kCalibWarps.
 template <class P>
 __device__ void repair_long_tile(const int32_t *__restrict__ row_ptr,
-                                 typename P::y_t *__restrict__ y, int32_t m, int32_t nnz,
-                                 int32_t L, int64_t t, int32_t start, int32_t stop, uint32_t info,
-                                 uint32_t *err, typename P::y_t *part, int32_t *cnt)
+                                 typename P::y_t *__restrict__ y, int32_t m,
+                                 int32_t start, int32_t stop, int32_t K, uint32_t *err,
+                                 typename P::y_t *part, int32_t *cnt, uint32_t *bits,
+                                 int32_t bits_words)
 {
     using Y = typename P::y_t;
     constexpr int CH = 8;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int32_t nseg = (int32_t)(info & kInfoSegMask);
-    const int64_t e = (t + 1) * (int64_t)L < nnz ? (t + 1) * (int64_t)L : nnz;
-    const bool cont = stop < m && (int64_t)__ldg(row_ptr + stop) < e;
-    const int32_t K = nseg - 1 - (cont ? 1 : 0);
-    if (K < 0 || K > L) {  // the same for every thread of the block
-        if (threadIdx.x == 0) atomicOr(err, SSSPMV_DEV_CALIB);
-        return;
-    }
     for (int32_t q = 1 + (int32_t)threadIdx.x; q <= K; q += (int32_t)blockDim.x)
-        part[q] = y[start + q];
+        cp_async_g2s(part + q, y + start + q);  // waited for after the count pass
     auto rp = [&](int32_t r) { return __ldg(row_ptr + (r < m ? r : m)); };
     // this warp's rows [r0, r1) of (start, stop), shares a multiple of 32
     const int32_t n = stop - start - 1;
     const int32_t per = ((n + kCalibWarps - 1) / kCalibWarps + 31) & ~31;
     const int32_t r0 = start + 1 + warp * per;
     const int32_t r1 = r0 + per < stop ? r0 + per : stop;
-    // walks [r0, r1): f(r, valid, non-empty) per row, chunk by chunk
+    const bool keep = (n + 31) / 32 <= bits_words;
+    // walks [r0, r1): f(first row of the chunk, r, valid, non-empty) per row,
+    // chunk by chunk (loads only chunks that hold rows of [r0, r1) or
+    // row_ptr[r1])
     auto walk = [&](auto &&f) {
         for (int32_t rb = r0; rb < r1; rb += 32 * CH) {
             int32_t pr[CH];
 #pragma unroll
-            for (int u = 0; u < CH; ++u) pr[u] = rp(rb + 32 * u + lane);
-            const int32_t tail = (lane == 31) ? rp(rb + 32 * CH) : 0;
+            for (int u = 0; u < CH; ++u) pr[u] = rb + 32 * u <= r1 ? rp(rb + 32 * u + lane) : 0;
+            const int32_t tail = (lane == 31 && rb + 32 * CH <= r1) ? rp(rb + 32 * CH) : 0;
 #pragma unroll
             for (int u = 0; u < CH; ++u) {
                 const int32_t r = rb + 32 * u + lane;
@@ -999,14 +1044,19 @@ __device__ void repair_long_tile(const int32_t *__restrict__ row_ptr,
                 int32_t nx = __shfl_down_sync(FULL, pr[u], 1);
                 if (lane == 31) nx = (u < CH - 1) ? lead : tail;
                 const bool valid = r < r1;
-                f(r, valid, valid && nx > pr[u]);
+                f(rb + 32 * u, r, valid, valid && nx > pr[u]);
             }
         }
     };
     int32_t mine = 0;
-    walk([&](int32_t, bool, bool ne) { mine += __popc(__ballot_sync(FULL, ne)); });
+    walk([&](int32_t rc, int32_t, bool, bool ne) {
+        const unsigned mask = __ballot_sync(FULL, ne);
+        mine += __popc(mask);
+        if (keep && lane == 0 && rc < r1) bits[(rc - (start + 1)) >> 5] = mask;
+    });
+    cp_async_wait_all();
     if (lane == 0) cnt[warp] = mine;
-    __syncthreads();  // counts and partials in place
+    __syncthreads();  // counts, flags and partials in place
     int32_t before = 0, total = 0;
     for (int w = 0; w < kCalibWarps; ++w) {
         const int32_t c = cnt[w];
@@ -1014,8 +1064,9 @@ __device__ void repair_long_tile(const int32_t *__restrict__ row_ptr,
         total += c;
     }
     if (threadIdx.x == 0 && total != K) atomicOr(err, SSSPMV_DEV_CALIB);
-    walk([&](int32_t r, bool valid, bool ne) {
-        const unsigned mask = __ballot_sync(FULL, ne);
+    // row r (valid: inside this warp's share) from its chunk's flags
+    auto place = [&](int32_t r, bool valid, unsigned mask) {
+        const bool ne = (mask >> lane) & 1u;
         const int32_t q = before + 1 + __popc(mask & ((1u << lane) - 1u));
         if (valid) {
             Y v = Y(0);
@@ -1026,8 +1077,16 @@ __device__ void repair_long_tile(const int32_t *__restrict__ row_ptr,
             y[r] = v;
         }
         before += __popc(mask);
-    });
-    __syncthreads();  // part and cnt are reused by the block's next tile
+    };
+    if (keep) {
+        for (int32_t rc = r0; rc < r1; rc += 32)
+            place(rc + lane, rc + lane < r1, bits[(rc - (start + 1)) >> 5]);
+    } else {
+        walk([&](int32_t, int32_t r, bool valid, bool ne) {
+            place(r, valid, __ballot_sync(FULL, ne));
+        });
+    }
+    __syncthreads();  // part, cnt and bits are reused by the block's next tile
 }
 
 // the batch matrix holding global tile t: the last one whose first tile is
@@ -1058,219 +1117,303 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
     Y *__restrict__ y = static_cast<Y *>(a.y);
     const int64_t ntiles = BATCHED ? (int64_t)__ldg(a.totals) : a.ntiles;
     const int64_t nbunches = BATCHED ? (int64_t)__ldg(a.totals + 1) : a.nbunches;
+    // ---- re-arrangement of dirty tiles (Sec. 3.2, checking prediction).
+    // Kernel (b) appended every dirty tile it left speculative to a list
+    // (the paper's speculator, in any order).  The tile role's warps stride
+    // over the list, consecutive entries going to consecutive blocks, and read
+    // up to 32 of their entries and tile flags in one round of loads.  A tile
+    // over more than kLongRepairRows rows is re-arranged by a whole block: for
+    // a single matrix, by the synchronizer and zeroing blocks once their own
+    // work is done (block b takes the long tiles among t = b (mod their
+    // count), found from the tile offsets, so that the long tiles at the
+    // sparse end of a matrix go to consecutive blocks); in a batch, by the
+    // tile-role block whose warp meets it in the list.
+    // a block's long tiles: index, rows [start, stop], inner partials
+    __shared__ int32_t s_long[kLongListCap], s_lst[kLongListCap], s_lsp[kLongListCap],
+        s_lK[kLongListCap];
+    __shared__ int32_t s_nlong, s_cnt[kCalibWarps];
+    int64_t count = (int64_t)*(volatile const uint32_t *)a.dirty_count;
+    if (count > ntiles) count = ntiles;  // kernel (b) appends each tile at most once
+    // the matrix data of global tile t (in a batch: of its matrix)
+    struct Tile {
+        const int32_t *row_ptr;
+        Y *y;
+        int32_t m, nnz, start, stop;
+        int64_t t;  // in its matrix
+    };
+    auto tile_of = [&](int64_t t) -> Tile {
+        if constexpr (BATCHED) {
+            const int32_t mi = batch_matrix_of_tile(a.mats, a.count, t);
+            const BatchMat *mm = a.mats + mi;
+            const int32_t tb = __ldg(&mm->tile_base);
+            const int32_t *to = a.tile_offset + tb + mi;  // the matrix's offsets
+            return Tile{ldg_ptr(&mm->row_ptr),
+                        static_cast<Y *>(ldg_ptr(const_cast<void *const *>(&mm->y))),
+                        __ldg(&mm->m), __ldg(&mm->nnz), __ldg(to + (t - tb)),
+                        __ldg(to + (t - tb) + 1), t - tb};
+        } else {
+            return Tile{a.row_ptr, y, a.m, a.nnz, __ldg(a.tile_offset + t),
+                        __ldg(a.tile_offset + t + 1), t};
+        }
+    };
+    // an entry must name a dirty tile that kernel (b) did not resolve
+    auto listed_ok = [&](int64_t t, uint32_t info) {
+        return t >= 0 && t < ntiles && (info & kInfoDirty) && !(info & kInfoResolved);
+    };
+    // the block's long tiles, kept in s_long: the first warp's buffer takes
+    // the partials, the other warps' buffers the non-empty flags
+    Y *bpart = reinterpret_cast<Y *>(calib_smem);
+    uint32_t *bits = reinterpret_cast<uint32_t *>(bpart + (a.L + 1));
+    const int32_t bits_words =
+        (int32_t)((size_t)(kCalibWarps - 1) * (size_t)(a.L + 1) * sizeof(Y) / 4);
+    auto repair_kept = [&]() {
+        __syncthreads();  // s_long complete
+        const int nl = s_nlong < kLongListCap ? s_nlong : kLongListCap;
+        for (int i = 0; i < nl; ++i) {
+            Tile T;
+            if constexpr (BATCHED) T = tile_of(s_long[i]);  // the matrix's arrays
+            else T = Tile{a.row_ptr, y, a.m, a.nnz, s_lst[i], s_lsp[i], s_long[i]};
+            if (s_lK[i] >= 0)  // the same for every thread of the block
+                repair_long_tile<P>(T.row_ptr, T.y, T.m, s_lst[i], s_lsp[i], s_lK[i], a.err,
+                                    bpart, s_cnt, bits, bits_words);
+        }
+        __syncthreads();
+    };
+    // (single matrix) the long dirty tiles among t = b0 (mod nb), in rounds
+    // of kLongListCap tiles, four per thread with their loads in flight
+    // together (a round cannot overflow s_long)
+    auto repair_long_strided = [&](int64_t b0, int64_t nb) {
+        constexpr int U = kLongListCap / (kCalibWarps * 32);
+        const int64_t per_round = (int64_t)kLongListCap * nb;
+        for (int64_t base = b0; base < ntiles; base += per_round) {
+            if (threadIdx.x == 0) s_nlong = 0;
+            __syncthreads();
+            int32_t st[U], sp[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t t = base + (int64_t)(threadIdx.x + u * kCalibWarps * 32) * nb;
+                st[u] = t < ntiles ? __ldg(a.tile_offset + t) : 0;
+                sp[u] = t < ntiles ? __ldg(a.tile_offset + t + 1) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t t = base + (int64_t)(threadIdx.x + u * kCalibWarps * 32) * nb;
+                if (t < ntiles && sp[u] - st[u] > kLongRepairRows) {
+                    // the flags and row_ptr[stop] in one round
+                    const uint32_t info = __ldg(a.tile_info + t);
+                    const int32_t rstop = __ldg(a.row_ptr + (sp[u] < a.m ? sp[u] : a.m));
+                    if (listed_ok(t, info)) {
+                        const int32_t K = inner_partials(a.m, a.nnz, a.L, t, sp[u], rstop, info);
+                        if (K < 0) {
+                            atomicOr(a.err, SSSPMV_DEV_CALIB);
+                        } else {
+                            const int slot = atomicAdd(&s_nlong, 1);
+                            s_long[slot] = (int32_t)t;
+                            s_lst[slot] = st[u];
+                            s_lsp[slot] = sp[u];
+                            s_lK[slot] = K;
+                        }
+                    }
+                }
+            }
+            repair_kept();
+        }
+    };
     int blk = blockIdx.x;
-
-    if (blk < a.nblk_tiles) {
-        // ---- re-arrangement of dirty tiles (Sec. 3.2, checking prediction).
-        // Kernel (b) appended every dirty tile it left speculative to a list
-        // (the paper's speculator, in any order); the warps of this role
-        // stride over it, consecutive entries going to consecutive blocks,
-        // and read up to 32 of their entries and tile flags in one round of
-        // loads.  A dirty tile over more than kLongRepairRows rows is
-        // deferred to its block, which re-arranges it with all its warps at
-        // the end.
-        __shared__ int64_t s_long[kLongListCap];
-        __shared__ uint32_t s_linfo[kLongListCap];
-        __shared__ int32_t s_nlong, s_cnt[kCalibWarps];
+    if (blk < a.nblk_sync + a.nblk_zero) {
+        if (blk < a.nblk_sync) {
+            // ---- synchronization (Alg. 1's synchronization step, on the GPU):
+            // the run of bunches sharing a first row adds into that row, plus the
+            // tail partial the bunch before the run left for it.  A warp covers
+            // 32 bunches, one per lane; runs are summed by a segmented warp scan
+            // and a run that goes on past the window is finished by this warp.
+            const double *sv = static_cast<const double *>(a.sync_val);
+            const double *tv = static_cast<const double *>(a.tail_val);
+            // (in a batch, runs are keyed by matrix and row: bunches of different
+            // matrices never share a row)
+            auto key_of = [&](int64_t ww) -> int64_t {
+                const int64_t r = __ldg(a.sync_idx + ww);
+                if constexpr (BATCHED) return ((int64_t)__ldg(a.bunch_mat + ww) << 32) | r;
+                else return r;
+            };
+            // windows of 32 bunches, one per warp, strided over the role's warps
+            for (int64_t wi = (int64_t)blk * kCalibWarps + warp; wi * 32 < nbunches;
+                 wi += (int64_t)a.nblk_sync * kCalibWarps) {
+                const int64_t base = wi * 32;
+                const int64_t w = base + lane;
+                const bool valid = w < nbunches;
+                const int64_t kw = valid ? key_of(w) : -1;
+                const int32_t r = (int32_t)(kw & 0xffffffff);
+                int64_t kprev = __shfl_up_sync(FULL, kw, 1);
+                if (lane == 0) kprev = (valid && w > 0) ? key_of(w - 1) : -1;
+                const bool lead = valid && (w == 0 || kprev != kw);
+                Y *__restrict__ yw = y;  // y and m of this lane's bunch's matrix
+                int32_t mw = a.m;
+                if constexpr (BATCHED) {
+                    if (valid) {
+                        const BatchMat *mm = a.mats + (kw >> 32);
+                        yw = static_cast<Y *>(ldg_ptr(const_cast<void *const *>(&mm->y)));
+                        mw = __ldg(&mm->m);
+                    }
+                }
+                // this bunch's partial and the tail partial the bunch before it left
+                // (used if this lane leads its run), loaded in the same round as the
+                // keys
+                double C = valid ? sv[w] : 0.0;
+                double tprev = 0.0;
+                if (valid && w > 0) {
+                    const int32_t f = __ldg(a.tail_flag + w - 1);
+                    const double v = tv[w - 1];  // read unconditionally, kept only if flagged
+                    tprev = f ? v : 0.0;
+                }
+                const unsigned lmask = __ballot_sync(FULL, lead);
+                if (lmask == 0) continue;  // the whole window continues a run led earlier
+                const int firstlead = __ffs(lmask) - 1;
+                const bool owned = valid && lane >= firstlead;
+                // segmented inclusive sum over runs (heads: leaders and invalid lanes)
+                const bool head = lead || !valid;
+                const unsigned hmask = __ballot_sync(FULL, head) | 1u;
+                const unsigned le = hmask & ((lane == 31) ? FULL : ((2u << lane) - 1u));
+                const int first = 31 - __clz(le);
+        #pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const double o = __shfl_up_sync(FULL, C, d);
+                    if (lane - d >= first) C += o;
+                }
+                // does this lane's run go on to the next bunch?
+                bool next_same;
+                const bool next_lead = __shfl_down_sync(FULL, lead, 1);
+                const bool next_valid = __shfl_down_sync(FULL, valid, 1);
+                if (lane < 31) next_same = next_valid && !next_lead;
+                else next_same = valid && w + 1 < nbunches && key_of(w + 1) == kw;
+                const double tlead = __shfl_sync(FULL, tprev, first);  // of the run's leader
+                if (owned && !next_same) {
+                    const double total = C + tlead;
+                    if (r >= 0 && r < mw) yw[r] = scaled_store_value(yw, r, (Y)total, a.alpha, a.beta, a.axpby);
+                    else atomicOr(a.err, SSSPMV_DEV_RANGE);
+                }
+                const bool open = __shfl_sync(FULL, owned && next_same, 31);
+                if (open) {  // the last run continues past the window (long rows)
+                    const int64_t kk = __shfl_sync(FULL, kw, 31);
+                    const int32_t rr = (int32_t)(kk & 0xffffffff);
+                    const double csum = __shfl_sync(FULL, C, 31);
+                    const double ctail = __shfl_sync(FULL, tlead, 31);
+                    // eight windows of 32 bunches per round trip of loads (a row of
+                    // 10^6 entries spans hundreds of bunches); each lane still adds
+                    // its bunches in increasing order, so the sum does not change
+                    constexpr int U = 8;
+                    double acc = 0.0;
+                    for (int64_t b2 = base + 32;; b2 += 32 * U) {
+                        bool in[U];
+        #pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const int64_t ww = b2 + 32 * u + lane;
+                            in[u] = ww < nbunches && key_of(ww) == kk;
+                        }
+                        bool full = true;
+        #pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            if (in[u]) acc += sv[b2 + 32 * u + lane];
+                            full = full && __all_sync(FULL, in[u]);
+                        }
+                        if (!full) break;
+                    }
+        #pragma unroll
+                    for (int d = 16; d >= 1; d >>= 1) acc += __shfl_xor_sync(FULL, acc, d);
+                    Y *__restrict__ yr =
+                        reinterpret_cast<Y *>(__shfl_sync(FULL, (unsigned long long)yw, 31));
+                    const int32_t mr = __shfl_sync(FULL, mw, 31);
+                    if (lane == 0) {
+                        const double total = csum + acc + ctail;
+                        if (rr >= 0 && rr < mr)
+                            yr[rr] = scaled_store_value(yr, rr, (Y)total, a.alpha, a.beta, a.axpby);
+                        else atomicOr(a.err, SSSPMV_DEV_RANGE);
+                    }
+                }
+            }
+        } else {
+            blk -= a.nblk_sync;
+            // ---- rows before tile_offset[0] are empty and covered by no tile (in
+            // a batch: each matrix's, the role's warps striding over the matrices)
+            if constexpr (BATCHED) {
+                for (int32_t mi = blk * kCalibWarps + warp; mi < a.count;
+                     mi += a.nblk_zero * kCalibWarps) {  // a warp per matrix
+                    const BatchMat *mm = a.mats + mi;
+                    const int32_t r0 = __ldg(a.tile_offset + __ldg(&mm->tile_base) + mi);
+                    Y *__restrict__ ym = static_cast<Y *>(ldg_ptr(const_cast<void *const *>(&mm->y)));
+                    for (int32_t r = lane; r < r0; r += 32)
+                        ym[r] = scaled_store_value(ym, r, Y(0), a.alpha, a.beta, a.axpby);
+                }
+            } else {
+                const int32_t r0 = __ldg(a.tile_offset);
+                for (int64_t r = (int64_t)blk * blockDim.x + threadIdx.x; r < r0;
+                     r += (int64_t)a.nblk_zero * blockDim.x)
+                    y[r] = scaled_store_value(y, r, Y(0), a.alpha, a.beta, a.axpby);
+            }
+        }
+        // these blocks are done long before the tile role's warps
+        if constexpr (!BATCHED) {
+            if (count > 0) repair_long_strided(blockIdx.x, (int64_t)a.nblk_sync + a.nblk_zero);
+        }
+        return;
+    }
+    blk -= a.nblk_sync + a.nblk_zero;
+    const int64_t nw = (int64_t)a.nblk_tiles * kCalibWarps;
+    if constexpr (BATCHED) {
         if (threadIdx.x == 0) s_nlong = 0;
         __syncthreads();
-        const int64_t nw = (int64_t)a.nblk_tiles * kCalibWarps;
-        int64_t count = (int64_t)*(volatile const uint32_t *)a.dirty_count;
-        if (count > ntiles) count = ntiles;  // kernel (b) appends each tile at most once
-        // the matrix data of global tile t (in a batch: of its matrix)
-        struct Tile {
-            const int32_t *row_ptr;
-            Y *y;
-            int32_t m, nnz, start, stop;
-            int64_t t;  // in its matrix
-        };
-        auto tile_of = [&](int64_t t) -> Tile {
+    }
+    // the other dirty tiles, a warp each (in a batch, long ones are kept for
+    // the block while there is room)
+    for (int64_t i0 = (int64_t)warp * a.nblk_tiles + blk; i0 < count; i0 += nw * 32) {
+        const int64_t il = i0 + (int64_t)lane * nw;
+        const int64_t tl = il < count ? (int64_t)__ldg(a.dirty_list + il) : -1;
+        const bool okt = tl >= 0 && tl < ntiles;
+        const uint32_t infl = okt ? __ldg(a.tile_info + tl) : 0u;
+        // (single matrix) the window's tile offsets in the same round
+        int32_t st_l = 0, sp_l = 0;
+        if (!BATCHED && okt) {
+            st_l = __ldg(a.tile_offset + tl);
+            sp_l = __ldg(a.tile_offset + tl + 1);
+        }
+        const bool good = listed_ok(tl, infl);
+        if (il < count && !good) atomicOr(a.err, SSSPMV_DEV_CALIB);
+        // (single matrix) long tiles were taken by the scan above
+        unsigned todo = __ballot_sync(FULL, good && (BATCHED || sp_l - st_l <= kLongRepairRows));
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t t = __shfl_sync(FULL, tl, src);
+            const uint32_t info = __shfl_sync(FULL, infl, src);
+            Tile T;
             if constexpr (BATCHED) {
-                const int32_t mi = batch_matrix_of_tile(a.mats, a.count, t);
-                const BatchMat *mm = a.mats + mi;
-                const int32_t tb = __ldg(&mm->tile_base);
-                const int32_t *to = a.tile_offset + tb + mi;  // the matrix's offsets
-                return Tile{ldg_ptr(&mm->row_ptr),
-                            static_cast<Y *>(ldg_ptr(const_cast<void *const *>(&mm->y))),
-                            __ldg(&mm->m), __ldg(&mm->nnz), __ldg(to + (t - tb)),
-                            __ldg(to + (t - tb) + 1), t - tb};
-            } else {
-                return Tile{a.row_ptr, y, a.m, a.nnz, __ldg(a.tile_offset + t),
-                            __ldg(a.tile_offset + t + 1), t};
-            }
-        };
-        for (int64_t i0 = (int64_t)warp * a.nblk_tiles + blk; i0 < count; i0 += nw * 32) {
-            const int64_t il = i0 + (int64_t)lane * nw;
-            const int64_t tl = il < count ? (int64_t)__ldg(a.dirty_list + il) : -1;
-            const bool okt = tl >= 0 && tl < ntiles;
-            const uint32_t infl = okt ? __ldg(a.tile_info + tl) : 0u;
-            // (single matrix) the window's tile offsets in the same round
-            int32_t st_l = 0, sp_l = 0;
-            if (!BATCHED && okt) {
-                st_l = __ldg(a.tile_offset + tl);
-                sp_l = __ldg(a.tile_offset + tl + 1);
-            }
-            // an entry must name a dirty tile that kernel (b) did not resolve
-            const bool good = okt && (infl & kInfoDirty) && !(infl & kInfoResolved);
-            if (il < count && !good) atomicOr(a.err, SSSPMV_DEV_CALIB);
-            unsigned todo = __ballot_sync(FULL, good);
-            while (todo) {
-                const int src = __ffs(todo) - 1;
-                todo &= todo - 1;
-                const int64_t t = __shfl_sync(FULL, tl, src);
-                const uint32_t info = __shfl_sync(FULL, infl, src);
-                Tile T;
-                if constexpr (BATCHED) {
-                    T = tile_of(t);
-                } else {
-                    T = Tile{a.row_ptr, y, a.m, a.nnz, __shfl_sync(FULL, st_l, src),
-                             __shfl_sync(FULL, sp_l, src), t};
-                }
+                T = tile_of(t);
                 if (T.stop - T.start > kLongRepairRows) {
                     int slot = 0;
                     if (lane == 0) slot = atomicAdd(&s_nlong, 1);
                     slot = __shfl_sync(FULL, slot, 0);
                     if (slot < kLongListCap) {
+                        const int32_t rstop = __ldg(T.row_ptr + (T.stop < T.m ? T.stop : T.m));
+                        const int32_t K = inner_partials(T.m, T.nnz, a.L, T.t, T.stop, rstop, info);
                         if (lane == 0) {
-                            s_long[slot] = t;
-                            s_linfo[slot] = info;
+                            s_long[slot] = (int32_t)t;
+                            s_lst[slot] = T.start;
+                            s_lsp[slot] = T.stop;
+                            s_lK[slot] = K;
+                            if (K < 0) atomicOr(a.err, SSSPMV_DEV_CALIB);
                         }
                         continue;
                     }
                 }
-                repair_dirty_tile<P>(T.row_ptr, T.y, T.m, T.nnz, a.L, T.t, T.start, T.stop, info,
-                                     a.err, lane, part);
+            } else {
+                T = Tile{a.row_ptr, y, a.m, a.nnz, __shfl_sync(FULL, st_l, src),
+                         __shfl_sync(FULL, sp_l, src), t};
             }
+            repair_dirty_tile<P>(T.row_ptr, T.y, T.m, T.nnz, a.L, T.t, T.start, T.stop, info,
+                                 a.err, lane, part);
         }
-        __syncthreads();
-        const int nlong = s_nlong < kLongListCap ? s_nlong : kLongListCap;
-        Y *bpart = reinterpret_cast<Y *>(calib_smem);  // every warp's buffer is free now
-        for (int i = 0; i < nlong; ++i) {
-            const Tile T = tile_of(s_long[i]);
-            repair_long_tile<P>(T.row_ptr, T.y, T.m, T.nnz, a.L, T.t, T.start, T.stop, s_linfo[i],
-                                a.err, bpart, s_cnt);
-        }
-        return;
     }
-    blk -= a.nblk_tiles;
-    if (blk < a.nblk_sync) {
-        // ---- synchronization (Alg. 1's synchronization step, on the GPU):
-        // the run of bunches sharing a first row adds into that row, plus the
-        // tail partial the bunch before the run left for it.  A warp covers
-        // 32 bunches, one per lane; runs are summed by a segmented warp scan
-        // and a run that goes on past the window is finished by this warp.
-        const double *sv = static_cast<const double *>(a.sync_val);
-        const double *tv = static_cast<const double *>(a.tail_val);
-        // (in a batch, runs are keyed by matrix and row: bunches of different
-        // matrices never share a row)
-        auto key_of = [&](int64_t ww) -> int64_t {
-            const int64_t r = __ldg(a.sync_idx + ww);
-            if constexpr (BATCHED) return ((int64_t)__ldg(a.bunch_mat + ww) << 32) | r;
-            else return r;
-        };
-        const int64_t base = ((int64_t)blk * kCalibWarps + warp) * 32;
-        const int64_t w = base + lane;
-        const bool valid = w < nbunches;
-        const int64_t kw = valid ? key_of(w) : -1;
-        const int32_t r = (int32_t)(kw & 0xffffffff);
-        int64_t kprev = __shfl_up_sync(FULL, kw, 1);
-        if (lane == 0) kprev = (valid && w > 0) ? key_of(w - 1) : -1;
-        const bool lead = valid && (w == 0 || kprev != kw);
-        Y *__restrict__ yw = y;  // y and m of this lane's bunch's matrix
-        int32_t mw = a.m;
-        if constexpr (BATCHED) {
-            if (valid) {
-                const BatchMat *mm = a.mats + (kw >> 32);
-                yw = static_cast<Y *>(ldg_ptr(const_cast<void *const *>(&mm->y)));
-                mw = __ldg(&mm->m);
-            }
-        }
-        const unsigned lmask = __ballot_sync(FULL, lead);
-        if (lmask == 0) return;  // the whole window continues a run led earlier
-        const int firstlead = __ffs(lmask) - 1;
-        const bool owned = valid && lane >= firstlead;
-        // segmented inclusive sum over runs (heads: leaders and invalid lanes)
-        const bool head = lead || !valid;
-        const unsigned hmask = __ballot_sync(FULL, head) | 1u;
-        const unsigned le = hmask & ((lane == 31) ? FULL : ((2u << lane) - 1u));
-        const int first = 31 - __clz(le);
-        double C = valid ? sv[w] : 0.0;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const double o = __shfl_up_sync(FULL, C, d);
-            if (lane - d >= first) C += o;
-        }
-        // does this lane's run go on to the next bunch?
-        bool next_same;
-        const bool next_lead = __shfl_down_sync(FULL, lead, 1);
-        const bool next_valid = __shfl_down_sync(FULL, valid, 1);
-        if (lane < 31) next_same = next_valid && !next_lead;
-        else next_same = valid && w + 1 < nbunches && key_of(w + 1) == kw;
-        if (owned && !next_same) {
-            const int64_t wl = base + first;  // the run's leader
-            double total = C;
-            if (wl > 0 && __ldg(a.tail_flag + wl - 1)) total += tv[wl - 1];
-            if (r >= 0 && r < mw) yw[r] = scaled_store_value(yw, r, (Y)total, a.alpha, a.beta, a.axpby);
-            else atomicOr(a.err, SSSPMV_DEV_RANGE);
-        }
-        const bool open = __shfl_sync(FULL, owned && next_same, 31);
-        if (open) {  // the last run continues past the window (long rows)
-            const int64_t kk = __shfl_sync(FULL, kw, 31);
-            const int32_t rr = (int32_t)(kk & 0xffffffff);
-            const double csum = __shfl_sync(FULL, C, 31);
-            const int64_t wl = base + __shfl_sync(FULL, first, 31);
-            // eight windows of 32 bunches per round trip of loads (a row of
-            // 10^6 entries spans hundreds of bunches); each lane still adds
-            // its bunches in increasing order, so the sum does not change
-            constexpr int U = 8;
-            double acc = 0.0;
-            for (int64_t b2 = base + 32;; b2 += 32 * U) {
-                bool in[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int64_t ww = b2 + 32 * u + lane;
-                    in[u] = ww < nbunches && key_of(ww) == kk;
-                }
-                bool full = true;
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if (in[u]) acc += sv[b2 + 32 * u + lane];
-                    full = full && __all_sync(FULL, in[u]);
-                }
-                if (!full) break;
-            }
-#pragma unroll
-            for (int d = 16; d >= 1; d >>= 1) acc += __shfl_xor_sync(FULL, acc, d);
-            Y *__restrict__ yr =
-                reinterpret_cast<Y *>(__shfl_sync(FULL, (unsigned long long)yw, 31));
-            const int32_t mr = __shfl_sync(FULL, mw, 31);
-            if (lane == 0) {
-                double total = csum + acc;
-                if (wl > 0 && __ldg(a.tail_flag + wl - 1)) total += tv[wl - 1];
-                if (rr >= 0 && rr < mr)
-                    yr[rr] = scaled_store_value(yr, rr, (Y)total, a.alpha, a.beta, a.axpby);
-                else atomicOr(a.err, SSSPMV_DEV_RANGE);
-            }
-        }
-        return;
-    }
-    blk -= a.nblk_sync;
-    // ---- rows before tile_offset[0] are empty and covered by no tile (in
-    // a batch: each matrix's, the blocks striding over the matrices)
-    if constexpr (BATCHED) {
-        for (int32_t mi = blk; mi < a.count; mi += a.nblk_zero) {
-            const BatchMat *mm = a.mats + mi;
-            const int32_t r0 = __ldg(a.tile_offset + __ldg(&mm->tile_base) + mi);
-            Y *__restrict__ ym = static_cast<Y *>(ldg_ptr(const_cast<void *const *>(&mm->y)));
-            for (int32_t r = threadIdx.x; r < r0; r += blockDim.x)
-                ym[r] = scaled_store_value(ym, r, Y(0), a.alpha, a.beta, a.axpby);
-        }
-    } else {
-        const int32_t r0 = __ldg(a.tile_offset);
-        for (int64_t r = (int64_t)blk * blockDim.x + threadIdx.x; r < r0;
-             r += (int64_t)a.nblk_zero * blockDim.x)
-            y[r] = scaled_store_value(y, r, Y(0), a.alpha, a.beta, a.axpby);
-    }
+    if constexpr (BATCHED) repair_kept();
 }
 
 }  // namespace ssspmv
