@@ -1014,14 +1014,12 @@ __device__ void repair_long_tile(const int32_t *__restrict__ row_ptr,
                                  typename P::y_t *__restrict__ y, int32_t m,
                                  int32_t start, int32_t stop, int32_t K, uint32_t *err,
                                  typename P::y_t *part, int32_t *cnt, uint32_t *bits,
-                                 int32_t bits_words)
+                                 int32_t bits_words, int32_t *stage, int32_t stage_chunks)
 {
     using Y = typename P::y_t;
-    constexpr int CH = 8;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int32_t q = 1 + (int32_t)threadIdx.x; q <= K; q += (int32_t)blockDim.x)
         cp_async_g2s(part + q, y + start + q);  // waited for after the count pass
-    auto rp = [&](int32_t r) { return __ldg(row_ptr + (r < m ? r : m)); };
     // this warp's rows [r0, r1) of (start, stop), shares a multiple of 32
     const int32_t n = stop - start - 1;
     const int32_t per = ((n + kCalibWarps - 1) / kCalibWarps + 31) & ~31;
@@ -1029,23 +1027,23 @@ __device__ void repair_long_tile(const int32_t *__restrict__ row_ptr,
     const int32_t r1 = r0 + per < stop ? r0 + per : stop;
     const bool keep = (n + 31) / 32 <= bits_words;
     // walks [r0, r1): f(first row of the chunk, r, valid, non-empty) per row,
-    // chunk by chunk (loads only chunks that hold rows of [r0, r1) or
-    // row_ptr[r1])
+    // chunk by chunk.  The row pointers of stage_chunks chunks (and the one
+    // after them) are copied at a time into the warp's staging buffer by
+    // asynchronous copies, so many are in flight without holding registers.
+    int32_t *st = stage + warp * (32 * stage_chunks + 4);
     auto walk = [&](auto &&f) {
-        for (int32_t rb = r0; rb < r1; rb += 32 * CH) {
-            int32_t pr[CH];
-#pragma unroll
-            for (int u = 0; u < CH; ++u) pr[u] = rb + 32 * u <= r1 ? rp(rb + 32 * u + lane) : 0;
-            const int32_t tail = (lane == 31 && rb + 32 * CH <= r1) ? rp(rb + 32 * CH) : 0;
-#pragma unroll
-            for (int u = 0; u < CH; ++u) {
-                const int32_t r = rb + 32 * u + lane;
-                const int32_t lead = __shfl_sync(FULL, pr[u < CH - 1 ? u + 1 : CH - 1], 0);
-                int32_t nx = __shfl_down_sync(FULL, pr[u], 1);
-                if (lane == 31) nx = (u < CH - 1) ? lead : tail;
-                const bool valid = r < r1;
-                f(rb + 32 * u, r, valid, valid && nx > pr[u]);
+        for (int32_t rb = r0; rb < r1; rb += 32 * stage_chunks) {
+            const int32_t nr = r1 - rb < 32 * stage_chunks ? r1 - rb : 32 * stage_chunks;
+            for (int32_t i = lane; i <= nr; i += 32)
+                cp_async_g2s(st + i, row_ptr + (rb + i < m ? rb + i : m));
+            cp_async_wait_all();
+            __syncwarp();
+            for (int32_t c = 0; c < nr; c += 32) {
+                const int32_t i = c + lane;
+                const bool valid = i < nr;
+                f(rb + c, rb + i, valid, valid && st[i + 1] > st[i]);
             }
+            __syncwarp();  // the buffer is refilled next
         }
     };
     int32_t mine = 0;
@@ -1161,11 +1159,18 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
         return t >= 0 && t < ntiles && (info & kInfoDirty) && !(info & kInfoResolved);
     };
     // the block's long tiles, kept in s_long: the first warp's buffer takes
-    // the partials, the other warps' buffers the non-empty flags
+    // the partials; the other warps' buffers stage row pointers (up to 16
+    // chunks of 32 per warp and pass, leaving at least 1,024 words) and hold
+    // the non-empty flags
     Y *bpart = reinterpret_cast<Y *>(calib_smem);
     uint32_t *bits = reinterpret_cast<uint32_t *>(bpart + (a.L + 1));
-    const int32_t bits_words =
+    const int32_t rest_words =
         (int32_t)((size_t)(kCalibWarps - 1) * (size_t)(a.L + 1) * sizeof(Y) / 4);
+    int32_t stage_chunks = ((rest_words - 1024) / kCalibWarps - 4) / 32;
+    if (stage_chunks > 16) stage_chunks = 16;
+    const int32_t stage_words = kCalibWarps * (32 * stage_chunks + 4);
+    const int32_t bits_words = rest_words - stage_words;
+    int32_t *stage = reinterpret_cast<int32_t *>(bits + bits_words);
     auto repair_kept = [&]() {
         __syncthreads();  // s_long complete
         const int nl = s_nlong < kLongListCap ? s_nlong : kLongListCap;
@@ -1175,7 +1180,7 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
             else T = Tile{a.row_ptr, y, a.m, a.nnz, s_lst[i], s_lsp[i], s_long[i]};
             if (s_lK[i] >= 0)  // the same for every thread of the block
                 repair_long_tile<P>(T.row_ptr, T.y, T.m, s_lst[i], s_lsp[i], s_lK[i], a.err,
-                                    bpart, s_cnt, bits, bits_words);
+                                    bpart, s_cnt, bits, bits_words, stage, stage_chunks);
         }
         __syncthreads();
     };
