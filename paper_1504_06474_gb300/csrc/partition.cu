@@ -88,8 +88,10 @@ __global__ void __launch_bounds__(kPartitionThreads)
             const uint32_t tlo = (lo[u] + (L - 1u)) / L;
             const uint32_t thi = (hi[u] + (L - 1u)) / L;
             const bool longrow = thi - tlo > 8u;
-            if (!longrow)
+            if (!longrow) {
+#pragma unroll 1
                 for (uint32_t t = tlo; t < thi; ++t) tile_offset[t] = (int32_t)r;
+            }
             unsigned lm = __ballot_sync(0xffffffffu, longrow);
             while (lm) {
                 const int src = __ffs(lm) - 1;

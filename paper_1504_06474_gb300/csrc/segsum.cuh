@@ -1265,6 +1265,9 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
                 // (used if this lane leads its run), loaded in the same round as the
                 // keys
                 double C = valid ? sv[w] : 0.0;
+                // (lane 31) the next window's first key, in the same round
+                const int64_t knext =
+                    (lane == 31 && valid && w + 1 < nbunches) ? key_of(w + 1) : -2;
                 double tprev = 0.0;
                 if (valid && w > 0) {
                     const int32_t f = __ldg(a.tail_flag + w - 1);
@@ -1290,7 +1293,7 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
                 const bool next_lead = __shfl_down_sync(FULL, lead, 1);
                 const bool next_valid = __shfl_down_sync(FULL, valid, 1);
                 if (lane < 31) next_same = next_valid && !next_lead;
-                else next_same = valid && w + 1 < nbunches && key_of(w + 1) == kw;
+                else next_same = valid && w + 1 < nbunches && knext == kw;
                 const double tlead = __shfl_sync(FULL, tprev, first);  // of the run's leader
                 if (owned && !next_same) {
                     const double total = C + tlead;
