@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(kPartitionThreads)
     }
     // every lane of a warp runs the same iterations (the ballots need them)
     const uint32_t warp0 = i0 - lane;
+    bool spread = false;
     for (uint32_t r0 = i0; warp0 + (r0 - i0) < mu; r0 += 4u * stride) {
         uint32_t lo[4], hi[4];
 #pragma unroll
@@ -75,11 +76,8 @@ __global__ void __launch_bounds__(kPartitionThreads)
             lo[u] = in ? (uint32_t)__ldg(row_ptr + r) : 0u;
             hi[u] = in ? (uint32_t)__ldg(row_ptr + r + 1) : 0u;
         }
-        // 32 consecutive empty rows (sampled: the first of the four chunks):
-        // flag for kernel (b)'s schedule (cleared by kernel (c) of the call
-        // before)
-        if (__ballot_sync(0xffffffffu, lo[0] != hi[0] || r0 >= mu) == 0u && lane == 0)
-            err[kWordSpread] = 1u;
+        // 32 consecutive empty rows (sampled: the first of the four chunks)
+        spread = spread || __ballot_sync(0xffffffffu, lo[0] != hi[0] || r0 >= mu) == 0u;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             // tiles t with lo <= t*L < hi; a row spanning many tiles is
@@ -103,6 +101,9 @@ __global__ void __launch_bounds__(kPartitionThreads)
             }
         }
     }
+    // flag for kernel (b)'s schedule (cleared by kernel (c) of the call
+    // before), one store per block
+    if (__syncthreads_or(spread) && threadIdx.x == 0) err[kWordSpread] = 1u;
 }
 
 int partition_method(int32_t m, int64_t ntiles)
