@@ -1185,8 +1185,8 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
         __syncthreads();
     };
     // (single matrix) the long dirty tiles among t = b0 (mod nb), in rounds
-    // of kLongListCap tiles, four per thread with their loads in flight
-    // together (a round cannot overflow s_long)
+    // of kLongListCap tiles, kLongListCap / 256 per thread with their loads
+    // in flight together (a round cannot overflow s_long)
     auto repair_long_strided = [&](int64_t b0, int64_t nb) {
         constexpr int U = kLongListCap / (kCalibWarps * 32);
         const int64_t per_round = (int64_t)kLongListCap * nb;
@@ -1283,7 +1283,7 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
                 const unsigned hmask = __ballot_sync(FULL, head) | 1u;
                 const unsigned le = hmask & ((lane == 31) ? FULL : ((2u << lane) - 1u));
                 const int first = 31 - __clz(le);
-        #pragma unroll
+#pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
                     const double o = __shfl_up_sync(FULL, C, d);
                     if (lane - d >= first) C += o;
@@ -1313,20 +1313,20 @@ __global__ void __launch_bounds__(kCalibWarps * 32) calibrate_kernel(const Calib
                     double acc = 0.0;
                     for (int64_t b2 = base + 32;; b2 += 32 * U) {
                         bool in[U];
-        #pragma unroll
+#pragma unroll
                         for (int u = 0; u < U; ++u) {
                             const int64_t ww = b2 + 32 * u + lane;
                             in[u] = ww < nbunches && key_of(ww) == kk;
                         }
                         bool full = true;
-        #pragma unroll
+#pragma unroll
                         for (int u = 0; u < U; ++u) {
                             if (in[u]) acc += sv[b2 + 32 * u + lane];
                             full = full && __all_sync(FULL, in[u]);
                         }
                         if (!full) break;
                     }
-        #pragma unroll
+#pragma unroll
                     for (int d = 16; d >= 1; d >>= 1) acc += __shfl_xor_sync(FULL, acc, d);
                     Y *__restrict__ yr =
                         reinterpret_cast<Y *>(__shfl_sync(FULL, (unsigned long long)yw, 31));
