@@ -5,8 +5,9 @@ kernel (c) re-arranges nearly all of them with whole blocks (several per
 block), plus a run of 400,000 rows holding one tile's worth of entries: a tile
 over more rows than the block's non-empty flag area holds, whose second pass
 walks the row pointers again.  FP64 against the oracle's index artefacts and
-y (both dirty-tile variants, two tile widths); FP32 and a batch against the
-compensated bound of the reduced-precision tests.
+y (both dirty-tile variants, two tile widths) and split into tile-range
+shards; FP32 and a batch against the compensated bound of the
+reduced-precision tests.
 """
 import numpy as np
 import pytest
@@ -20,6 +21,7 @@ pytestmark = pytest.mark.gpu
 from test_gpu_batched import Batch, _C, _check_all  # noqa: E402
 from test_gpu_parity import check_case  # noqa: E402
 from test_gpu_reduced import _check, _run  # noqa: E402
+from test_gpu_shards import _ntiles, _run_shards  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -80,3 +82,12 @@ def test_long_tiles_in_a_batch(dev):
     ws = b.run(opts)
     assert C.ssspmv_device_status(ws) == 0
     _check_all(b, opts)
+
+
+def test_long_tiles_in_four_shards(dev):
+    from paper_1504_06474_gb300 import api
+    A, x = long_tile_matrix()
+    y = _run_shards(dev, A, x, api.split_tiles(_ntiles(A), 4))
+    yref, s = oracle.spmv_dot2(A.row_ptr, A.col, A.val, x)
+    assert np.all(np.abs(y - yref) <= 1e-13 * s)
+    assert np.all(y[s == 0] == 0.0)
